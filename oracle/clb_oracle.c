@@ -25,10 +25,14 @@
  *    image of the bottom one, which is the only wall the paper writes out.
  *  - Pressure columns ("consistent linear extrapolation", Sec. 3.2, details not
  *    given): after streaming, all nine populations of the inlet column are
- *      fbar_i(0,y) = f^eq_i(rho_in, u_b) + 2 f^neq_i(1,y) - f^neq_i(2,y),
- *      u_b = 2 u(1,y) - u(2,y),  f^neq = fbar - f^eq(rho, u)
- *    and the outlet mirrors it with rho_out and columns nx-2, nx-3.  The
- *    extrapolated f^neq carries no mass, so rho(0,y) = rho_in exactly.
+ *      fbar_i(0,y) = f^eq_i(rho_in, u_b) + f^neq_i(1,y),
+ *      u_b = 2 u(1,y) - u(2,y),  f^neq = fbar - f^eq(rho, u):
+ *    the velocity is extrapolated linearly from the two interior neighbours,
+ *    the non-equilibrium part is taken from the first one, and the density is
+ *    imposed; the outlet mirrors it with rho_out and columns nx-2, nx-3.
+ *    f^neq carries no mass, so rho(0,y) = rho_in exactly.  (Extrapolating
+ *    f^neq linearly too, 2 f^neq(1) - f^neq(2), amplifies the shortest
+ *    x-wavelength threefold and diverges at the outlet once tau ~ 30.)
  *  - Local Knudsen number (Sec. 3.2): Kn = Kn_out p_out / p taken per node
  *    with p = rho/3 at that node.
  *  - tau~_q in Eq. 21 is 1/s_v - 1/2, as the sentence after Eq. 21 defines it.
@@ -410,13 +414,12 @@ static void macro_of(const double f[9], double Fx, double Fy, double* rho, doubl
 static void pressure_rebuild(const oracle_params* p, const double f1[9], const double f2[9],
                              double rho_b, double out[9])
 {
-    double r1, u1x, u1y, r2, u2x, u2y, e1[9], e2[9], eb[9];
+    double r1, u1x, u1y, r2, u2x, u2y, e1[9], eb[9];
     macro_of(f1, p->gx, p->gy, &r1, &u1x, &u1y);
     macro_of(f2, p->gx, p->gy, &r2, &u2x, &u2y);
     oracle_feq(r1, u1x, u1y, e1);
-    oracle_feq(r2, u2x, u2y, e2);
     oracle_feq(rho_b, 2.0 * u1x - u2x, 2.0 * u1y - u2y, eb);
-    for (int i = 0; i < NQ; ++i) out[i] = eb[i] + 2.0 * (f1[i] - e1[i]) - (f2[i] - e2[i]);
+    for (int i = 0; i < NQ; ++i) out[i] = eb[i] + (f1[i] - e1[i]);
 }
 
 /* Steps 1-3 of a time step: streaming, walls, pressure columns. */

@@ -207,3 +207,16 @@ def test_knudsen_trend_of_slip(oracle_mod):
         o = s.observables()
         vals.append(o["u_slip"] / o["ux_prof"].mean())
     assert vals[0] < vals[1] < vals[2]
+
+
+def test_pressure_channel_stays_bounded_at_high_tau(oracle_mod):
+    """tau~ ~ 30 (Kn_out = 1, ny = 64): the pressure columns must not feed a
+    growing short-wave mode; the channel stays finite with a small transverse
+    velocity (a linear extrapolation of f^neq diverged here by step 1500)."""
+    p = oracle_mod.OracleParams(nx=401, ny=64, pressure=True, kn=1.0, rho_in=1.2, rho_out=1.0)
+    s = oracle_mod.OracleSim(p)
+    s.step(2500, 4)
+    rho, ux, uy = s.macro()
+    assert np.isfinite(rho).all()
+    assert np.abs(uy).max() < 0.05 * np.abs(ux).max()
+    assert rho.min() > 0.99 and rho.max() < 1.21
