@@ -1,0 +1,177 @@
+/*
+ * clb.h - C ABI of the GB300 (sm_103a) hot path of the cascaded lattice
+ * Boltzmann (CLB) method for 2D microchannel gas flow of Liu & He,
+ * "Numerical modelling of microchannel gas flows in the transition flow
+ * regime using the cascaded lattice Boltzmann method" (arXiv:1603.01955).
+ *
+ * One call of clb_step(sim, n) advances a straight channel by n time steps of
+ * the fused D2Q9 stream-and-collide sweep:
+ *   - streaming of the transformed populations fbar = f - S/2 (Sec. 2.1, Eq. 4-5);
+ *   - the cascaded central-moment collision with its body-force source
+ *     (Eq. 6-13), relaxation rates s3 = 1.1, s8 = 1.2 (Sec. 3);
+ *   - a relaxation rate per node from the Bosanquet effective viscosity at the
+ *     local Knudsen number (Sec. 2.2, Eq. 16-18; Sec. 3.2 Kn = Kn_out p_out/p);
+ *   - combined bounce-back/specular-reflection walls (Eq. 20) with r_b and
+ *     s6 = s7 = s_q of the modified second-order slip condition (Eq. 19, 21);
+ *   - periodic inlet/outlet (Sec. 3.1) or pressure inlet/outlet columns
+ *     rebuilt by linear extrapolation (Sec. 3.2).
+ *
+ * Geometry: nx nodes along the channel (x), ny across it (y).  The walls sit
+ * half a cell below row 0 and above row ny-1, so H = ny (Eq. 18's N).
+ *
+ * Conventions for every entry point:
+ *   - Device state is owned by the library; every host array is owned by the
+ *     caller, and a NULL output pointer skips that output.
+ *   - All device work is queued on the simulation's stream (the one given in
+ *     clb_opts, or one the library creates).  clb_step does not synchronise;
+ *     clb_observables, clb_get_state, clb_set_state and clb_sync do.
+ *   - Nothing is thrown across the ABI.  Each call returns a clb_status;
+ *     clb_last_error() gives a message for the last failure on the calling
+ *     thread.
+ *   - A simulation may be used from one host thread at a time.
+ */
+#ifndef CLB_H
+#define CLB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct clb_sim clb_sim; /* opaque */
+
+typedef enum {
+    CLB_OK = 0,
+    CLB_EINVAL = 1,   /* a parameter is out of range or inconsistent */
+    CLB_ENOMEM = 2,   /* device or host allocation failed */
+    CLB_ECUDA = 3,    /* a CUDA call failed (message has the CUDA error) */
+    CLB_ENUMERIC = 4, /* a NaN or Inf was seen in the fields */
+    CLB_ETIMEOUT = 5  /* reserved: a bounded device wait gave up */
+} clb_status;
+
+typedef enum {
+    CLB_DRIVE_BODY_FORCE = 0, /* periodic in x, constant body force G along x (Sec. 3.1) */
+    CLB_DRIVE_PRESSURE = 1    /* pressure inlet/outlet, drive_value = p_in/p_out (Sec. 3.2) */
+} clb_drive;
+
+typedef enum {
+    CLB_FP64 = 0,         /* populations stored and collided in FP64 (144 B per node update) */
+    CLB_FP32_SHIFTED = 1, /* FP32 deviations f - w_i rho_ref(x), FP32 collision (72 B) */
+    CLB_FP16_SCALED = 2,  /* reserved: 16-bit storage with a per-plane scale */
+    CLB_BF16_SCALED = 3   /* reserved */
+} clb_storage;
+
+/* Optional settings; clb_opts_default() fills the paper's values (Sec. 3). */
+typedef struct {
+    double b2;      /* second-order slip coefficient B2 (Eq. 19, 21); 0.55 */
+    double sigma;   /* TMAC sigma, used for r_b when r < 0 (Eq. 19, 21; B1 = 1 - 0.1817 sigma); 1.0 */
+    double s3, s8;  /* free relaxation rates; 1.1, 1.2 */
+    double rho_out; /* outlet density (pressure drive) or mean density (body force); 1.0 */
+    int storage;    /* clb_storage; CLB_FP32_SHIFTED */
+    int vec;        /* nodes per thread along x (1, 2 or 4 for FP32, 1 or 2 for FP64); 0 = default */
+    int block_x;    /* threads per block (multiple of 32, <= 1024); 0 = default 128 */
+    void* stream;   /* cudaStream_t to queue work on; NULL = a stream owned by the library */
+    /* Device allocator hooks (e.g. a framework's caching allocator); both NULL
+     * = cudaMalloc / cudaFree.  alloc returns NULL on failure. */
+    void* (*alloc)(size_t bytes, void* ctx);
+    void (*free)(void* ptr, void* ctx);
+    void* alloc_ctx;
+} clb_opts;
+
+void clb_opts_default(clb_opts* opts);
+
+/*
+ * Create a channel and set its initial state f = f^eq(rho_init(x), u = 0)
+ * (Eq. 11), with rho_init = rho_out (body force) or linear from
+ * rho_in = drive_value * rho_out at x = 0 to rho_out at x = nx-1 (pressure).
+ *
+ *   nx, ny      lattice nodes; nx >= 1 (body force) or nx >= 4 (pressure); 1 <= ny <= 65535
+ *   kn          Knudsen number (body force) or outlet Knudsen number Kn_out (pressure), > 0
+ *   a           Bosanquet rarefaction factor of Eq. 16 (the paper uses 2), >= 0
+ *   r           bounce-back fraction r_b in [0, 1] of Eq. 20; r < 0 = Eq. 21 from opts->sigma
+ *   drive       clb_drive
+ *   drive_value G (lattice acceleration) or p_in/p_out (> 0)
+ *   opts        NULL = defaults
+ *   out         receives the new simulation; NULL on failure
+ * Errors: CLB_EINVAL (ranges above), CLB_ENOMEM, CLB_ECUDA.
+ */
+clb_status clb_create(int nx, int ny, double kn, double a, double r, clb_drive drive,
+                      double drive_value, const clb_opts* opts, clb_sim** out);
+
+/* Advance n >= 0 time steps (Eq. 4-5 with the boundaries above).  Queued on
+ * the stream, returns without waiting.  Errors: CLB_EINVAL (n < 0, sim NULL),
+ * CLB_ECUDA (launch failure). */
+clb_status clb_step(clb_sim* sim, int64_t n);
+
+/* Scalars of the current state.  Densities and velocities are taken per node
+ * from the populations of the last completed step (Eq. 12-13). */
+typedef struct {
+    double mass_flow;  /* m = mean over x of sum_y rho u_x (Sec. 3.2) */
+    double q_norm;     /* Q = sum_y u_x / (F H^2 sqrt(RT/2)/p) (Sec. 3.1, body force),
+                          or S = m / m_ns (Sec. 3.2, pressure; m_ns = no-slip isothermal flow
+                          with the unreduced viscosity) */
+    double u_slip;     /* u_x at the profile column extrapolated linearly from the first two
+                          rows to each wall, mean of both walls */
+    double residual;   /* |m(t) - m(t_prev)| / |m(t)| against the previous clb_observables
+                          call; -1 on the first call */
+    double total_mass; /* sum of rho over all nodes */
+    double ux_max;     /* max_y u_x at the profile column (Sec. 3.2 u_x,max) */
+    int64_t step;      /* time steps completed */
+} clb_scalars;
+
+/*
+ * Observables (Sec. 3.1, 3.2), reduced on the GPU in FP64 and copied to host
+ * arrays.  profile_col: column of the velocity profiles; -1 = outlet
+ * (nx-1, pressure) or column 0 (body force).  Outputs (each may be NULL):
+ *   s          scalars above
+ *   ux_prof    [ny]  u_x(y) at profile_col
+ *   uy_prof    [ny]  u_y(y) at profile_col
+ *   p_centre   [nx]  centreline pressure p = rho/3 (middle row, or mean of the two middle rows)
+ *   dp_nonlin  [nx]  (p_centre - p_l)/p_out, p_l = p_in - (p_in - p_out) x/(nx-1)
+ *   m_of_x     [nx]  sum_y rho u_x per column
+ * Synchronises the stream.  Errors: CLB_EINVAL, CLB_ECUDA, CLB_ENUMERIC (a
+ * NaN/Inf density or velocity was found; outputs are still written).
+ */
+clb_status clb_observables(clb_sim* sim, int profile_col, clb_scalars* s, double* ux_prof,
+                           double* uy_prof, double* p_centre, double* dp_nonlin, double* m_of_x);
+
+/* Copy the populations out / in, as FP64 host arrays [9][ny][nx], index
+ * (i*ny + y)*nx + x, holding the post-collision populations f~_i (Eq. 4) of
+ * the last completed step, whatever the storage.  Direction i follows Eq. 1:
+ * e0 = (0,0), e1..e4 = (1,0), (0,1), (-1,0), (0,-1), e5..e8 = (1,1), (-1,1),
+ * (-1,-1), (1,-1).  Synchronises the stream.  A transient device buffer of
+ * 72*nx*ny bytes is taken through the allocator for the copy. */
+clb_status clb_get_state(clb_sim* sim, double* host_f);
+clb_status clb_set_state(clb_sim* sim, const double* host_f);
+
+/* Description of a simulation. */
+typedef struct {
+    int nx, ny;
+    int pitch;            /* elements per stored row (includes halo and padding) */
+    int storage;          /* clb_storage */
+    int vec, block_x;     /* launch shape of the sweep */
+    int drive;            /* clb_drive */
+    double bytes_per_node;/* algorithmic bytes moved per node update: 18 * element size */
+    double sv, sq;        /* s_v, s_q (Eq. 18, 21) at Kn (body force) or Kn_out (pressure) */
+    double r;             /* r_b in use */
+    double kn, a, g, rho_in, rho_out;
+    int64_t step;
+    void* stream;         /* the cudaStream_t in use */
+} clb_info_t;
+clb_status clb_info(const clb_sim* sim, clb_info_t* info);
+
+/* Wait for all queued work of the simulation. */
+clb_status clb_sync(clb_sim* sim);
+
+/* Release everything the simulation owns; NULL is accepted. */
+clb_status clb_destroy(clb_sim* sim);
+
+/* Message for the last failing call on this thread ("" if none). */
+const char* clb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CLB_H */

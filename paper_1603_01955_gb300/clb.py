@@ -1,0 +1,251 @@
+"""Python binding of the C ABI in ``include/clb.h`` (ctypes; marshalling only).
+
+The functions ``clb_create``, ``clb_step``, ``clb_observables``,
+``clb_get_state``, ``clb_set_state``, ``clb_info``, ``clb_sync`` and
+``clb_destroy`` have the names and arguments of the C entry points; every step
+of the computation runs in the CUDA library.  ``Channel`` wraps one simulation
+with PyTorch supplying the device memory (its caching allocator) and the stream
+(the current stream of the device).
+
+There is no fallback: if ``libclb_gb300.so`` is missing or cannot be loaded,
+importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+CLB_OK, CLB_EINVAL, CLB_ENOMEM, CLB_ECUDA, CLB_ENUMERIC, CLB_ETIMEOUT = range(6)
+CLB_DRIVE_BODY_FORCE, CLB_DRIVE_PRESSURE = 0, 1
+CLB_FP64, CLB_FP32_SHIFTED, CLB_FP16_SCALED, CLB_BF16_SCALED = 0, 1, 2, 3
+
+STORAGE = {"fp64": CLB_FP64, "fp32s": CLB_FP32_SHIFTED, "fp16s": CLB_FP16_SCALED, "bf16s": CLB_BF16_SCALED}
+DRIVE = {"body_force": CLB_DRIVE_BODY_FORCE, "pressure": CLB_DRIVE_PRESSURE}
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class clb_opts(C.Structure):
+    _fields_ = [
+        ("b2", C.c_double), ("sigma", C.c_double), ("s3", C.c_double), ("s8", C.c_double),
+        ("rho_out", C.c_double), ("storage", C.c_int), ("vec", C.c_int), ("block_x", C.c_int),
+        ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
+    ]
+
+
+class clb_scalars(C.Structure):
+    _fields_ = [
+        ("mass_flow", C.c_double), ("q_norm", C.c_double), ("u_slip", C.c_double),
+        ("residual", C.c_double), ("total_mass", C.c_double), ("ux_max", C.c_double),
+        ("step", C.c_int64),
+    ]
+
+
+class clb_info_t(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int), ("ny", C.c_int), ("pitch", C.c_int), ("storage", C.c_int),
+        ("vec", C.c_int), ("block_x", C.c_int), ("drive", C.c_int),
+        ("bytes_per_node", C.c_double), ("sv", C.c_double), ("sq", C.c_double), ("r", C.c_double),
+        ("kn", C.c_double), ("a", C.c_double), ("g", C.c_double), ("rho_in", C.c_double),
+        ("rho_out", C.c_double), ("step", C.c_int64), ("stream", C.c_void_p),
+    ]
+
+
+class CLBError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"clb status {status}: {msg}")
+        self.status = status
+
+
+def _load():
+    path = _build.LIB
+    if _build.stale():
+        # compile in place when nvcc is at hand; otherwise fail loudly below
+        try:
+            _build.build_library()
+        except Exception as e:  # noqa: BLE001
+            raise ImportError(f"CUDA library {path} is missing or stale and could not be built: {e}") from e
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library {path} not found; run __graft_entry__.build()")
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    D = C.POINTER(C.c_double)
+    lib.clb_opts_default.argtypes = [C.POINTER(clb_opts)]
+    lib.clb_opts_default.restype = None
+    lib.clb_create.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_int, C.c_double,
+                               C.POINTER(clb_opts), C.POINTER(P)]
+    lib.clb_step.argtypes = [P, C.c_int64]
+    lib.clb_observables.argtypes = [P, C.c_int, C.POINTER(clb_scalars), D, D, D, D, D]
+    lib.clb_get_state.argtypes = [P, P]
+    lib.clb_set_state.argtypes = [P, P]
+    lib.clb_info.argtypes = [P, C.POINTER(clb_info_t)]
+    lib.clb_sync.argtypes = [P]
+    lib.clb_destroy.argtypes = [P]
+    lib.clb_last_error.argtypes = []
+    lib.clb_last_error.restype = C.c_char_p
+    for name in ("clb_create", "clb_step", "clb_observables", "clb_get_state", "clb_set_state",
+                 "clb_info", "clb_sync", "clb_destroy"):
+        getattr(lib, name).restype = C.c_int
+    return lib
+
+
+lib = _load()
+LIB_PATH = _build.LIB
+
+
+def _check(st):
+    if st != CLB_OK:
+        raise CLBError(st, lib.clb_last_error().decode(errors="replace"))
+    return st
+
+
+def _dptr(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+# ------------------------------------------------------------ C-ABI mirror
+
+def clb_opts_default() -> clb_opts:
+    o = clb_opts()
+    lib.clb_opts_default(C.byref(o))
+    return o
+
+
+def clb_create(nx, ny, kn, a, r, drive, drive_value, opts: clb_opts | None = None):
+    h = C.c_void_p()
+    _check(lib.clb_create(int(nx), int(ny), float(kn), float(a), float(r), int(drive), float(drive_value),
+                          C.byref(opts) if opts is not None else None, C.byref(h)))
+    return h
+
+
+def clb_step(sim, n):
+    return _check(lib.clb_step(sim, int(n)))
+
+
+def clb_observables(sim, profile_col, s, ux_prof, uy_prof, p_centre, dp_nonlin, m_of_x, check=True):
+    st = lib.clb_observables(sim, int(profile_col), C.byref(s) if s is not None else None, _dptr(ux_prof),
+                             _dptr(uy_prof), _dptr(p_centre), _dptr(dp_nonlin), _dptr(m_of_x))
+    return _check(st) if check else st
+
+
+def clb_get_state(sim, host_ptr):
+    return _check(lib.clb_get_state(sim, C.c_void_p(host_ptr)))
+
+
+def clb_set_state(sim, host_ptr):
+    return _check(lib.clb_set_state(sim, C.c_void_p(host_ptr)))
+
+
+def clb_info(sim) -> clb_info_t:
+    i = clb_info_t()
+    _check(lib.clb_info(sim, C.byref(i)))
+    return i
+
+
+def clb_sync(sim):
+    return _check(lib.clb_sync(sim))
+
+
+def clb_destroy(sim):
+    return _check(lib.clb_destroy(sim))
+
+
+# ------------------------------------------------------------ convenience
+
+class Channel:
+    """One channel on the current CUDA device.
+
+    drive='body_force': periodic in x, ``drive_value`` = G (lattice acceleration).
+    drive='pressure': inlet/outlet, ``drive_value`` = p_in/p_out, ``kn`` = Kn_out.
+    ``r`` < 0 takes r_b from Eq. 21 with ``sigma``.
+    """
+
+    def __init__(self, nx, ny, kn, a=2.0, r=-1.0, drive="body_force", drive_value=0.0, storage="fp32s",
+                 vec=0, block_x=0, b2=0.55, sigma=1.0, s3=1.1, s8=1.2, rho_out=1.0, stream=None,
+                 torch_allocator=True):
+        import torch
+
+        self.nx, self.ny = int(nx), int(ny)
+        dev = torch.cuda.current_device()
+        self._stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        o = clb_opts_default()
+        o.b2, o.sigma, o.s3, o.s8, o.rho_out = b2, sigma, s3, s8, rho_out
+        o.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+        o.vec, o.block_x = int(vec), int(block_x)
+        o.stream = C.c_void_p(self._stream.cuda_stream)
+        if torch_allocator:
+            s = self._stream
+
+            def _alloc(n, ctx):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(n), dev, s)
+                except Exception:  # noqa: BLE001 - reported to the library as NULL
+                    return None
+
+            def _free(p, ctx):
+                torch.cuda.caching_allocator_delete(int(p))
+
+            self._hooks = (ALLOC_FN(_alloc), FREE_FN(_free))
+            o.alloc, o.free = self._hooks
+        d = DRIVE[drive] if isinstance(drive, str) else int(drive)
+        self.sim = clb_create(nx, ny, kn, a, r, d, drive_value, o)
+
+    def close(self):
+        if getattr(self, "sim", None):
+            clb_destroy(self.sim)
+            self.sim = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def stream(self):
+        return self._stream
+
+    def step(self, n=1):
+        clb_step(self.sim, n)
+
+    def sync(self):
+        clb_sync(self.sim)
+
+    def info(self) -> dict:
+        i = clb_info(self.sim)
+        return {k: getattr(i, k) for k, _ in clb_info_t._fields_ if k != "stream"}
+
+    def state(self) -> np.ndarray:
+        f = np.empty((9, self.ny, self.nx), np.float64)
+        clb_get_state(self.sim, f.ctypes.data)
+        return f
+
+    def set_state(self, f) -> None:
+        f = np.ascontiguousarray(f, dtype=np.float64).reshape(9, self.ny, self.nx)
+        clb_set_state(self.sim, f.ctypes.data)
+
+    def observables(self, profile_col=-1, check=True) -> dict:
+        s = clb_scalars()
+        ux = np.zeros(self.ny)
+        uy = np.zeros(self.ny)
+        pc = np.zeros(self.nx)
+        dp = np.zeros(self.nx)
+        mx = np.zeros(self.nx)
+        st = clb_observables(self.sim, profile_col, s, ux, uy, pc, dp, mx, check=check)
+        out = {k: getattr(s, k) for k, _ in clb_scalars._fields_}
+        out.update(ux_prof=ux, uy_prof=uy, p_centre=pc, dp_nonlin=dp, m_of_x=mx, status=st)
+        return out

@@ -1,0 +1,204 @@
+// Device-side arithmetic of the cascaded lattice Boltzmann (CLB) collision of
+// Liu & He (arXiv:1603.01955), Sec. 2, written for GB300 (sm_103a).
+//
+// Every routine works on deviations d_i = f_i - w_i R from a reference density
+// R (w_i the D2Q9 rest weights 4/9, 1/9, 1/36).  The moments' reference parts
+// cancel analytically, so the braces of Eq. 7 only ever combine small numbers
+// and FP32 keeps its precision; with R = 0 the same code is the plain form.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "clb_internal.h"
+
+namespace clb {
+
+// D2Q9 rest weights: Eq. 11 at u = 0 through the closed-form inverse of Eq. 10.
+template <typename R> struct Wt {
+    static constexpr R w0 = R(4.0 / 9.0);
+    static constexpr R wa = R(1.0 / 9.0);   // axis directions 1..4
+    static constexpr R wd = R(1.0 / 36.0);  // diagonal directions 5..8
+};
+
+__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+
+// Per-thread copies of the launch constants in the compute type.
+template <typename R> struct KC {
+    R s3_12, s8_4;    // s3/12, s8/4
+    R sv_4, sq_4;     // constant s_v/4, s_q/4 (body-force channel)
+    R A, B, A316, CA; // pressure channel: tau = A/(rho+B); 3/(16A); pi B2 A/4
+    R hfx, hfy;       // F/2
+    R fx, fy;         // F
+    R r, rc;          // r_b, 1 - r_b
+    R ref0, slope;    // R(x) = ref0 + slope x
+    R sha, shd;       // shift added to a value pulled from column x-1: -w slope
+    R drho_in, drho_out;
+    __device__ __forceinline__ void load(const SweepArgs& a) {
+        s3_12 = R(a.s3 / 12.0);
+        s8_4 = R(a.s8 / 4.0);
+        sv_4 = R(a.sv / 4.0);
+        sq_4 = R(a.sq / 4.0);
+        A = R(a.rate_A);
+        B = R(a.rate_B);
+        A316 = R(3.0 / (16.0 * a.rate_A));
+        CA = R(a.rate_C * a.rate_A);
+        hfx = R(0.5 * a.gx);
+        hfy = R(0.5 * a.gy);
+        fx = R(a.gx);
+        fy = R(a.gy);
+        r = R(a.r);
+        rc = R(1.0 - a.r);
+        ref0 = R(a.ref0);
+        slope = R(a.ref_slope);
+        sha = R(-a.ref_slope / 9.0);
+        shd = R(-a.ref_slope / 36.0);
+        drho_in = R(a.drho_in);
+        drho_out = R(a.drho_out);
+    }
+};
+
+// Inverse of the moment matrix T of Eq. 10 in closed form: populations from the
+// nine raw moments m0..m8 (1, x, y, xx+yy, xx-yy, xy, xxy, xyy, xxyy).
+template <typename R>
+__device__ __forceinline__ void tinv_apply(const R m[9], R f[9]) {
+    const R q = R(0.25);
+    f[0] = m[0] - m[3] + m[8];
+    const R c = m[3] - R(2) * m[8];
+    f[1] = q * (c + m[4] + R(2) * (m[1] - m[7]));
+    f[3] = q * (c + m[4] - R(2) * (m[1] - m[7]));
+    f[2] = q * (c - m[4] + R(2) * (m[2] - m[6]));
+    f[4] = q * (c - m[4] - R(2) * (m[2] - m[6]));
+    f[5] = q * (m[5] + m[6] + m[7] + m[8]);
+    f[6] = q * (-m[5] + m[6] - m[7] + m[8]);
+    f[7] = q * (m[5] - m[6] - m[7] + m[8]);
+    f[8] = q * (-m[5] - m[6] + m[7] + m[8]);
+}
+
+// Equilibrium of Eq. 11 minus w_i R, for a node with density rho = R + drho
+// and velocity (ux, uy).
+template <typename R>
+__device__ __forceinline__ void feq_dev(R drho, R rho, R ux, R uy, R f[9]) {
+    const R ux2 = ux * ux, uy2 = uy * uy, u2 = ux2 + uy2;
+    R m[9];
+    m[0] = drho;
+    m[1] = rho * ux;
+    m[2] = rho * uy;
+    m[3] = R(2.0 / 3.0) * drho + rho * u2;
+    m[4] = rho * (ux2 - uy2);
+    m[5] = rho * ux * uy;
+    m[6] = rho * uy * (R(1.0 / 3.0) + ux2);
+    m[7] = rho * ux * (R(1.0 / 3.0) + uy2);
+    m[8] = R(1.0 / 9.0) * drho + rho * (R(1.0 / 3.0) * u2 + ux2 * uy2);
+    tinv_apply(m, f);
+}
+
+// Density deviation and momentum sum e_i d_i of nine deviations.
+template <typename R>
+__device__ __forceinline__ void macro_dev(const R d[9], R& drho, R& jx, R& jy) {
+    const R p57 = d[5] - d[7], p86 = d[8] - d[6];
+    drho = d[0] + (d[1] + d[3]) + (d[2] + d[4]) + ((d[5] + d[7]) + (d[6] + d[8]));
+    jx = (d[1] - d[3]) + (p57 + p86);
+    jy = (d[2] - d[4]) + (p57 - p86);
+}
+
+// One cascaded collision (Eq. 4 with Eq. 6-9, 12-13), in place on the
+// deviations d relative to R = ref.  MODE_PERIODIC: body force F, constant
+// rates.  MODE_PRESSURE: no force, s_v and s_q from the local Knudsen number
+// Kn = Kn_out rho_out / rho (Sec. 3.2) through Eq. 18 and Eq. 21.
+template <typename R, int MODE>
+__device__ __forceinline__ void collide(R (&d)[9], R ref, const KC<R>& c) {
+    // raw moments of Eq. 8 (deviation parts)
+    const R a57 = d[5] + d[7], a68 = d[6] + d[8];
+    const R p57 = d[5] - d[7], p86 = d[8] - d[6];
+    const R kxy = a57 - a68;
+    const R kxxyy = a57 + a68;
+    const R kxxy = p57 - p86;
+    const R kxyy = p57 + p86;
+    const R s13 = d[1] + d[3], s24 = d[2] + d[4];
+    const R kxx = s13 + kxxyy;
+    const R kyy = s24 + kxxyy;
+    const R drho = d[0] + s13 + s24 + kxxyy;
+    const R jx = (d[1] - d[3]) + kxyy;
+    const R jy = (d[2] - d[4]) + kxxy;
+    // Eq. 12-13
+    const R rho = ref + drho;
+    const R irho = rcp(rho);
+    R ux = jx * irho, uy = jy * irho;
+    if (MODE == MODE_PERIODIC) {
+        ux += c.hfx;
+        uy += c.hfy;
+    }
+    // relaxation rates
+    R sv4, sq4;
+    if (MODE == MODE_PRESSURE) {
+        // tau = A/q, q = rho + B; 1/s_v = 1/2 + tau (Eq. 18);
+        // 1/s_q = 1/2 + 3/(16 tau) + (pi B2/4) tau (Eq. 21)
+        const R q = rho + c.B;
+        sv4 = R(0.25) * q * rcp(R(0.5) * q + c.A);
+        sq4 = R(0.25) * q * rcp(q * (R(0.5) + c.A316 * q) + c.CA);
+    } else {
+        sv4 = c.sv_4;
+        sq4 = c.sq_4;
+    }
+    const R ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
+    const R third = R(1.0 / 3.0) * ref;
+    const R kxxf = third + kxx;  // full k'_xx
+    const R kyyf = third + kyy;  // full k'_yy
+    // Eq. 7, in cascade order
+    R t3 = R(2.0 / 3.0) * drho - (kxx + kyy) + rho * (ux2 + uy2);
+    R t4 = rho * (ux2 - uy2) - (kxx - kyy);
+    R t5 = rho * uxy - kxy;
+    R t6 = R(2) * rho * ux2 * uy + kxxy - R(2) * ux * kxy - uy * kxxf;
+    R t7 = R(2) * rho * ux * uy2 + kxyy - R(2) * uy * kxy - ux * kyyf;
+    R t8 = R(1.0 / 9.0) * drho + R(3) * rho * ux2 * uy2 -
+           (kxxyy - R(2) * ux * kxyy - R(2) * uy * kxxy + ux2 * kyyf + uy2 * kxxf + R(4) * uxy * kxy);
+    if (MODE == MODE_PERIODIC) {
+        const R fx = c.fx, fy = c.fy;
+        t3 -= rho * (fx * ux + fy * uy);
+        t4 -= rho * (fx * ux - fy * uy);
+        t5 -= R(0.5) * rho * (fx * uy + fy * ux);
+        t6 -= R(0.5) * rho * (fy * ux2 + R(2) * fx * uxy);
+        t7 -= R(0.5) * rho * (fx * uy2 + R(2) * fy * uxy);
+        t8 -= rho * (fx * ux * uy2 + fy * uy * ux2);
+    }
+    const R g3 = c.s3_12 * t3;
+    const R g4 = sv4 * t4;
+    const R g5 = sv4 * t5;
+    const R h34p = R(3) * g3 + g4, h34m = R(3) * g3 - g4;
+    const R g6 = sq4 * t6 - R(0.5) * uy * h34p - R(2) * ux * g5;
+    const R g7 = sq4 * t7 - R(0.5) * ux * h34m - R(2) * uy * g5;
+    const R g8 = c.s8_4 * t8 - R(2) * g3 - R(0.5) * (uy2 * h34p + ux2 * h34m) - R(4) * uxy * g5 -
+                 R(2) * (uy * g6 + ux * g7);
+    // Eq. 6 (g0 = g1 = g2 = 0)
+    const R ca = g4 - g3, cb = -g3 - g4, ce = R(2) * g3 + g8;
+    d[0] += R(-4) * (g3 - g8);
+    d[1] += ca + R(2) * (g7 - g8);
+    d[3] += ca - R(2) * (g7 + g8);
+    d[2] += cb + R(2) * (g6 - g8);
+    d[4] += cb - R(2) * (g6 + g8);
+    d[5] += ce + g5 - g6 - g7;
+    d[6] += ce - g5 - g6 + g7;
+    d[7] += ce + g5 + g6 + g7;
+    d[8] += ce - g5 + g6 - g7;
+    if (MODE == MODE_PERIODIC) {
+        // source S = T^-1 S^ (Eq. 9-10)
+        const R fx = c.fx, fy = c.fy;
+        R m[9];
+        m[0] = R(0);
+        m[1] = rho * fx;
+        m[2] = rho * fy;
+        m[3] = R(2) * rho * (ux * fx + uy * fy);
+        m[4] = R(2) * rho * (ux * fx - uy * fy);
+        m[5] = rho * (ux * fy + uy * fx);
+        m[6] = rho * (fy * ux2 + R(2) * fx * uxy);
+        m[7] = rho * (fx * uy2 + R(2) * fy * uxy);
+        m[8] = R(2) * rho * uxy * (fx * uy + fy * ux);
+        R S[9];
+        tinv_apply(m, S);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) d[i] += S[i];
+    }
+}
+
+}  // namespace clb

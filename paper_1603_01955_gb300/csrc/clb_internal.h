@@ -1,0 +1,50 @@
+// Internal interface between the host runtime (runtime.cu) and the sweep
+// kernels (sweep.cu) of the CLB channel library.  Not part of the C ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace clb {
+
+enum : int { MODE_PERIODIC = 0, MODE_PRESSURE = 1 };
+
+// row_type bits: the first / last row touches the bottom / top wall.
+enum : uint8_t { ROW_BOTTOM = 1, ROW_TOP = 2 };
+// col_type bits: pressure inlet / outlet column (rebuilt before the collision),
+// and, for periodic x, the columns whose outgoing populations are mirrored into
+// the halo columns -1 and nx so that the next sweep needs no wrap-around.
+enum : uint8_t { COL_INLET = 1, COL_OUTLET = 2, COL_HALO_RIGHT = 4, COL_HALO_LEFT = 8 };
+
+// Everything one sweep launch needs (passed by value as a kernel argument).
+struct SweepArgs {
+    const void* fin;          // populations of the last step (post-collision)
+    void* fout;               // populations written by this step
+    int nx, ny;
+    int pitch;                // elements per stored row
+    int xoff;                 // element index of column 0 in a row (column -1 is xoff-1)
+    long long plane;          // elements per direction plane (= ny * pitch)
+    const uint8_t* row_type;  // [ny]
+    const uint8_t* col_type;  // [>= nx + 16], zero past nx-1
+    // collision (Eq. 7, 14, 18, 21)
+    double s3, s8;
+    double sv, sq;            // constant rates (body-force channel)
+    double rate_A, rate_B;    // pressure channel: tau = A / (rho + B)
+    double rate_C;            // pi * B2 / 4
+    double r;                 // CBBSR bounce-back fraction (Eq. 20)
+    double gx, gy;            // body force per unit mass (Eq. 9, 13)
+    // Stored values are deviations f - w_i R(x) from a reference density
+    // R(x) = ref0 + ref_slope * x (R = 0 for FP64 storage).
+    double ref0, ref_slope;
+    double drho_in, drho_out; // rho_in - R(0), rho_out - R(nx-1)
+};
+
+// Launch one sweep.  storage: clb_storage value; mode: MODE_*; vec: nodes per
+// thread along x; block_x: threads per block.
+cudaError_t launch_sweep(int storage, int mode, int vec, int block_x, const SweepArgs& a,
+                         cudaStream_t stream);
+
+// True if (storage, vec) has a compiled sweep.
+bool sweep_supported(int storage, int vec);
+
+}  // namespace clb

@@ -1,0 +1,652 @@
+// Host runtime and C ABI (include/clb.h) of the CLB channel library, plus the
+// small kernels around the sweep: initial equilibrium, state conversion, and
+// the FP64 observable reductions (Sec. 3.1, 3.2 of Liu & He, arXiv:1603.01955).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/clb.h"
+#include "clb_internal.h"
+
+using namespace clb;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+clb_status fail(clb_status st, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+#define CUDA_OR(expr)                                                                          \
+    do {                                                                                       \
+        cudaError_t e_ = (expr);                                                               \
+        if (e_ != cudaSuccess) return fail(CLB_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+    } while (0)
+
+constexpr double kPi = 3.14159265358979323846;
+
+// D2Q9 rest weights (Eq. 11 at u = 0) and directions (Eq. 1), host copies.
+__constant__ double c_w[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
+                              1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+__constant__ int c_ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+__constant__ int c_ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+
+// Observable scratch layout (doubles): per-column m(x), centre rho(x), column
+// sums of u_x, profile u_x(y), u_y(y), then per-block partial sums.
+struct ObsLayout {
+    size_t m, rc, prof_x, prof_y, part, total;
+    int nblocks;
+};
+
+constexpr int kObsCols = 32;  // columns per observable block
+constexpr int kObsRows = 8;   // row groups per observable block
+
+ObsLayout obs_layout(int nx, int ny) {
+    ObsLayout L;
+    L.nblocks = (nx + kObsCols - 1) / kObsCols;
+    L.m = 0;
+    L.rc = L.m + nx;
+    L.prof_x = L.rc + nx;
+    L.prof_y = L.prof_x + ny;
+    L.part = L.prof_y + ny;
+    L.total = L.part + 4 * (size_t)L.nblocks;
+    return L;
+}
+
+}  // namespace
+
+struct clb_sim {
+    int nx = 0, ny = 0, pitch = 0, xoff = 0, storage = 0, vec = 0, block_x = 0, drive = 0;
+    size_t elem = 0;        // bytes per stored element
+    long long plane = 0;    // elements per plane
+    size_t buf_bytes = 0;
+    void* buf[2] = {nullptr, nullptr};
+    int cur = 0;            // buffer holding the last completed step
+    uint8_t* row_type = nullptr;
+    uint8_t* col_type = nullptr;
+    size_t col_bytes = 0;
+    double* obs = nullptr;  // device scratch of the observable reductions
+    ObsLayout L{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    void* (*alloc)(size_t, void*) = nullptr;
+    void (*dealloc)(void*, void*) = nullptr;
+    void* alloc_ctx = nullptr;
+    // problem statement
+    double kn = 0, a = 0, r = 0, b2 = 0, sigma = 1, s3 = 0, s8 = 0, g = 0, rho_in = 1, rho_out = 1;
+    double sv = 0, sq = 0;
+    double ref0 = 0, ref_slope = 0;
+    int64_t step = 0;
+    bool have_prev = false;
+    double prev_mass_flow = 0;
+
+    void* dalloc(size_t bytes) {
+        if (bytes == 0) bytes = 256;
+        if (alloc) return alloc(bytes, alloc_ctx);
+        void* p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return p;
+    }
+    void dfree(void* p) {
+        if (!p) return;
+        if (dealloc)
+            dealloc(p, alloc_ctx);
+        else
+            cudaFree(p);
+    }
+    double ref_at(int x) const { return ref0 + ref_slope * (double)x; }
+};
+
+// ------------------------------------------------------------------ kernels
+
+namespace {
+
+template <class T>
+__global__ void init_kernel(T* f, int nx, int ny, int pitch, int xoff, long long plane, double rho_a,
+                            double rho_slope, double ref0, double ref_slope, int periodic) {
+    const long long n = 9LL * ny * nx;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(idx % nx);
+        const int y = (int)((idx / nx) % ny);
+        const int i = (int)(idx / ((long long)nx * ny));
+        // f^eq(rho_init(x), u = 0) = w_i rho_init(x) (Eq. 11), stored as a deviation from w_i R(x)
+        const double v = c_w[i] * ((rho_a + rho_slope * x) - (ref0 + ref_slope * x));
+        T* row = f + i * plane + (long long)y * pitch + xoff;
+        row[x] = T(v);
+        if (periodic) {
+            if (x == 0 && c_ex[i] < 0) row[nx] = T(v);
+            if (x == nx - 1 && c_ex[i] > 0) row[-1] = T(v);
+        }
+    }
+}
+
+template <class T>
+__global__ void to_canonical_kernel(const T* f, double* out, int nx, int ny, int pitch, int xoff, long long plane,
+                                    double ref0, double ref_slope) {
+    const long long n = 9LL * ny * nx;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(idx % nx);
+        const int y = (int)((idx / nx) % ny);
+        const int i = (int)(idx / ((long long)nx * ny));
+        const T* row = f + i * plane + (long long)y * pitch + xoff;
+        out[idx] = c_w[i] * (ref0 + ref_slope * x) + (double)row[x];
+    }
+}
+
+template <class T>
+__global__ void from_canonical_kernel(const double* in, T* f, int nx, int ny, int pitch, int xoff, long long plane,
+                                      double ref0, double ref_slope, int periodic) {
+    const long long n = 9LL * ny * nx;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(idx % nx);
+        const int y = (int)((idx / nx) % ny);
+        const int i = (int)(idx / ((long long)nx * ny));
+        const T v = T(in[idx] - c_w[i] * (ref0 + ref_slope * x));
+        T* row = f + i * plane + (long long)y * pitch + xoff;
+        row[x] = v;
+        if (periodic) {
+            if (x == 0 && c_ex[i] < 0) row[nx] = v;
+            if (x == nx - 1 && c_ex[i] > 0) row[-1] = v;
+        }
+    }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Per column: m(x) = sum_y rho u_x, centreline rho, sum_y u_x; the profiles at
+// one column; per block: partial sums of m, u_x, rho and a non-finite count.
+// Densities and velocities come from the post-collision populations of the
+// last step: the collision keeps rho and adds rho F to the momentum (Eq. 4, 9),
+// so rho u = sum_i e_i f~_i - rho F/2 is Eq. 13 at that time level.
+template <class T>
+__global__ void __launch_bounds__(kObsCols* kObsRows)
+    obs_kernel(const T* f, double* obs, ObsLayout L, int nx, int ny, int pitch, int xoff, long long plane,
+               double ref0, double ref_slope, double gx, double gy, int prof_col) {
+    __shared__ double sh[5][kObsRows][kObsCols];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int x = blockIdx.x * kObsCols + tx;
+    double m = 0, us = 0, mass = 0, rc = 0, bad = 0;
+    if (x < nx) {
+        const double ref = ref0 + ref_slope * x;
+        for (int y = ty; y < ny; y += kObsRows) {
+            const T* row = f + (long long)y * pitch + xoff + x;
+            double drho = 0, jx = 0, jy = 0;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const double v = (double)row[i * plane];
+                drho += v;
+                jx += c_ex[i] * v;
+                jy += c_ey[i] * v;
+            }
+            const double rho = ref + drho;
+            const double ux = (jx - 0.5 * rho * gx) / rho;
+            const double uy = (jy - 0.5 * rho * gy) / rho;
+            if (!isfinite(rho) || !isfinite(ux) || !isfinite(uy)) bad += 1;
+            m += rho * ux;
+            us += ux;
+            mass += rho;
+            // centreline: the middle row, or the mean of the two middle rows
+            if (ny & 1) {
+                if (y == (ny - 1) / 2) rc += rho;
+            } else if (y == ny / 2 - 1 || y == ny / 2) {
+                rc += 0.5 * rho;
+            }
+            if (x == prof_col) {
+                obs[L.prof_x + y] = ux;
+                obs[L.prof_y + y] = uy;
+            }
+        }
+    }
+    sh[0][ty][tx] = m;
+    sh[1][ty][tx] = us;
+    sh[2][ty][tx] = mass;
+    sh[3][ty][tx] = bad;
+    sh[4][ty][tx] = rc;
+    __syncthreads();
+    if (ty == 0) {  // one full warp: column totals in a fixed order, then block partials
+        double cm = 0, cu = 0, cmass = 0, cbad = 0, crc = 0;
+        for (int k = 0; k < kObsRows; ++k) {
+            cm += sh[0][k][tx];
+            cu += sh[1][k][tx];
+            cmass += sh[2][k][tx];
+            cbad += sh[3][k][tx];
+            crc += sh[4][k][tx];
+        }
+        if (x < nx) {
+            obs[L.m + x] = cm;
+            obs[L.rc + x] = crc;
+        }
+        cm = warp_sum(cm);
+        cu = warp_sum(cu);
+        cmass = warp_sum(cmass);
+        cbad = warp_sum(cbad);
+        if (tx == 0) {
+            obs[L.part + 4 * blockIdx.x + 0] = cm;
+            obs[L.part + 4 * blockIdx.x + 1] = cu;
+            obs[L.part + 4 * blockIdx.x + 2] = cmass;
+            obs[L.part + 4 * blockIdx.x + 3] = cbad;
+        }
+    }
+}
+
+// Sum the per-block partials in a fixed order (one warp), into part[0..3].
+__global__ void obs_final_kernel(double* obs, ObsLayout L) {
+    const int t = threadIdx.x;
+    double acc[4] = {0, 0, 0, 0};
+    for (int b = t; b < L.nblocks; b += 32)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[k] += obs[L.part + 4 * b + k];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[k] = warp_sum(acc[k]);
+    __syncwarp();
+    if (t == 0)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) obs[L.part + k] = acc[k];
+}
+
+int grid_for(long long n, int block) {
+    long long g = (n + block - 1) / block;
+    return (int)std::min<long long>(std::max<long long>(g, 1), 152LL * 32);
+}
+
+SweepArgs make_args(const clb_sim* s) {
+    SweepArgs a{};
+    a.fin = s->buf[s->cur];
+    a.fout = s->buf[s->cur ^ 1];
+    a.nx = s->nx;
+    a.ny = s->ny;
+    a.pitch = s->pitch;
+    a.xoff = s->xoff;
+    a.plane = s->plane;
+    a.row_type = s->row_type;
+    a.col_type = s->col_type;
+    a.s3 = s->s3;
+    a.s8 = s->s8;
+    a.sv = s->sv;
+    a.sq = s->sq;
+    // tau = sqrt(6/pi) N Kn_loc/(1 + a Kn_loc), Kn_loc = Kn_out rho_out/rho
+    //     = A/(rho + B), A = sqrt(6/pi) N Kn_out rho_out, B = a Kn_out rho_out
+    a.rate_A = std::sqrt(6.0 / kPi) * s->ny * s->kn * s->rho_out;
+    a.rate_B = s->a * s->kn * s->rho_out;
+    a.rate_C = kPi * s->b2 / 4.0;
+    a.r = s->r;
+    a.gx = s->drive == CLB_DRIVE_BODY_FORCE ? s->g : 0.0;
+    a.gy = 0.0;
+    a.ref0 = s->ref0;
+    a.ref_slope = s->ref_slope;
+    a.drho_in = s->rho_in - s->ref_at(0);
+    a.drho_out = s->rho_out - s->ref_at(s->nx - 1);
+    return a;
+}
+
+void rates_at(double kn, int ny, double a, double b2, double* sv, double* sq) {
+    // Eq. 18 and Eq. 21 (tau_q = 1/s_v - 1/2)
+    const double tau = std::sqrt(6.0 / kPi) * ny * kn / (1.0 + a * kn);
+    *sv = 1.0 / (0.5 + tau);
+    *sq = 1.0 / (0.5 + (3.0 + 4.0 * kPi * tau * tau * b2) / (16.0 * tau));
+}
+
+template <class T>
+cudaError_t launch_init(clb_sim* s, void* buf, double rho_a, double rho_slope) {
+    const long long n = 9LL * s->nx * s->ny;
+    init_kernel<T><<<grid_for(n, 256), 256, 0, s->stream>>>(
+        static_cast<T*>(buf), s->nx, s->ny, s->pitch, s->xoff, s->plane, rho_a, rho_slope, s->ref0, s->ref_slope,
+        s->drive == CLB_DRIVE_BODY_FORCE);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- C ABI
+
+extern "C" {
+
+void clb_opts_default(clb_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->b2 = 0.55;
+    o->sigma = 1.0;
+    o->s3 = 1.1;
+    o->s8 = 1.2;
+    o->rho_out = 1.0;
+    o->storage = CLB_FP32_SHIFTED;
+}
+
+const char* clb_last_error(void) { return g_err; }
+
+clb_status clb_destroy(clb_sim* s) {
+    if (!s) return CLB_OK;
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    s->dfree(s->buf[0]);
+    s->dfree(s->buf[1]);
+    s->dfree(s->row_type);
+    s->dfree(s->col_type);
+    s->dfree(s->obs);
+    if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+    delete s;
+    return CLB_OK;
+}
+
+clb_status clb_create(int nx, int ny, double kn, double a, double r, clb_drive drive, double drive_value,
+                      const clb_opts* opts, clb_sim** out) {
+    g_err[0] = 0;
+    if (!out) return fail(CLB_EINVAL, "clb_create: out is NULL");
+    *out = nullptr;
+    clb_opts o;
+    clb_opts_default(&o);
+    if (opts) o = *opts;
+    if (drive != CLB_DRIVE_BODY_FORCE && drive != CLB_DRIVE_PRESSURE)
+        return fail(CLB_EINVAL, "clb_create: unknown drive %d", (int)drive);
+    if (ny < 1 || ny > 65535) return fail(CLB_EINVAL, "clb_create: ny = %d outside 1..65535", ny);
+    if (nx < (drive == CLB_DRIVE_PRESSURE ? 4 : 1) || nx > (1 << 28))
+        return fail(CLB_EINVAL, "clb_create: nx = %d too small or too large for this drive", nx);
+    if (!(kn > 0) || !std::isfinite(kn)) return fail(CLB_EINVAL, "clb_create: Kn must be > 0");
+    if (!(a >= 0) || !std::isfinite(a)) return fail(CLB_EINVAL, "clb_create: a must be >= 0");
+    if (!std::isfinite(r) || r > 1) return fail(CLB_EINVAL, "clb_create: r must be in [0, 1] (or < 0 for Eq. 21)");
+    if (!std::isfinite(drive_value)) return fail(CLB_EINVAL, "clb_create: drive value not finite");
+    if (drive == CLB_DRIVE_PRESSURE && !(drive_value > 0))
+        return fail(CLB_EINVAL, "clb_create: pressure ratio must be > 0");
+    if (!(o.rho_out > 0) || !(o.b2 >= 0) || !(o.s3 > 0 && o.s3 < 2) || !(o.s8 > 0 && o.s8 < 2))
+        return fail(CLB_EINVAL, "clb_create: rho_out, b2, s3 or s8 out of range");
+    if (r < 0 && !(o.sigma > 0 && o.sigma <= 2)) return fail(CLB_EINVAL, "clb_create: sigma must be in (0, 2]");
+    if (o.storage != CLB_FP64 && o.storage != CLB_FP32_SHIFTED)
+        return fail(CLB_EINVAL, "clb_create: storage %d not available", o.storage);
+    if ((o.alloc == nullptr) != (o.free == nullptr))
+        return fail(CLB_EINVAL, "clb_create: alloc and free hooks must be given together");
+    int vec = o.vec ? o.vec : (o.storage == CLB_FP64 ? 2 : 4);
+    if (!sweep_supported(o.storage, vec)) return fail(CLB_EINVAL, "clb_create: vec = %d not available", vec);
+    int block_x = o.block_x ? o.block_x : 128;
+    if (block_x < 32 || block_x > 256 || block_x % 32)
+        return fail(CLB_EINVAL, "clb_create: block_x = %d must be a multiple of 32 in 32..256", block_x);
+
+    clb_sim* s = new (std::nothrow) clb_sim;
+    if (!s) return fail(CLB_ENOMEM, "clb_create: host allocation failed");
+    s->nx = nx;
+    s->ny = ny;
+    s->storage = o.storage;
+    s->vec = vec;
+    s->block_x = block_x;
+    s->drive = drive;
+    s->kn = kn;
+    s->a = a;
+    s->b2 = o.b2;
+    s->sigma = o.sigma;
+    s->s3 = o.s3;
+    s->s8 = o.s8;
+    s->rho_out = o.rho_out;
+    s->alloc = o.alloc;
+    s->dealloc = o.free;
+    s->alloc_ctx = o.alloc_ctx;
+    if (drive == CLB_DRIVE_BODY_FORCE) {
+        s->g = drive_value;
+        s->rho_in = o.rho_out;
+    } else {
+        s->g = 0;
+        s->rho_in = drive_value * o.rho_out;
+    }
+    // Eq. 21 with sigma_v = (2 - sigma)/sigma and B1 = 1 - 0.1817 sigma (Sec. 3)
+    s->r = r >= 0 ? r : 1.0 / (1.0 + (1.0 - 0.1817 * o.sigma) * (2.0 - o.sigma) / o.sigma * std::sqrt(kPi / 6.0));
+    rates_at(kn, ny, a, o.b2, &s->sv, &s->sq);
+
+    // reference density of the stored deviations: the initial profile
+    if (o.storage == CLB_FP64) {
+        s->ref0 = 0;
+        s->ref_slope = 0;
+    } else if (drive == CLB_DRIVE_PRESSURE) {
+        s->ref0 = s->rho_in;
+        s->ref_slope = (s->rho_out - s->rho_in) / (double)(nx - 1);
+    } else {
+        s->ref0 = s->rho_out;
+        s->ref_slope = 0;
+    }
+
+    s->elem = (o.storage == CLB_FP64) ? 8 : 4;
+    const int align = (int)(128 / s->elem);
+    s->xoff = align;
+    s->pitch = ((s->xoff + nx + 16 + align - 1) / align) * align;
+    s->plane = (long long)ny * s->pitch;
+    s->buf_bytes = (size_t)9 * s->plane * s->elem;
+    s->L = obs_layout(nx, ny);
+    s->col_bytes = (size_t)((nx + 16 + 15) / 16) * 16;
+
+    if (o.stream) {
+        s->stream = static_cast<cudaStream_t>(o.stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaError_t e = cudaGetLastError();
+            delete s;
+            return fail(CLB_ECUDA, "clb_create: cudaStreamCreate: %s", cudaGetErrorString(e));
+        }
+        s->own_stream = true;
+    }
+
+    s->buf[0] = s->dalloc(s->buf_bytes);
+    s->buf[1] = s->dalloc(s->buf_bytes);
+    s->row_type = static_cast<uint8_t*>(s->dalloc(ny));
+    s->col_type = static_cast<uint8_t*>(s->dalloc(s->col_bytes));
+    s->obs = static_cast<double*>(s->dalloc(s->L.total * sizeof(double)));
+    if (!s->buf[0] || !s->buf[1] || !s->row_type || !s->col_type || !s->obs) {
+        clb_destroy(s);
+        return fail(CLB_ENOMEM, "clb_create: device allocation of %zu bytes failed", 2 * s->buf_bytes);
+    }
+
+    // node-type masks (separable: row type x column type)
+    std::vector<uint8_t> rt(ny, 0), ct(s->col_bytes, 0);
+    rt[0] |= ROW_BOTTOM;
+    rt[ny - 1] |= ROW_TOP;
+    if (drive == CLB_DRIVE_PRESSURE) {
+        ct[0] |= COL_INLET;
+        ct[nx - 1] |= COL_OUTLET;
+    } else {
+        ct[0] |= COL_HALO_RIGHT;
+        ct[nx - 1] |= COL_HALO_LEFT;
+    }
+    clb_status st = CLB_OK;
+    auto chk = [&](cudaError_t e, const char* what) {
+        if (e != cudaSuccess && st == CLB_OK) st = fail(CLB_ECUDA, "clb_create: %s: %s", what, cudaGetErrorString(e));
+    };
+    chk(cudaMemcpyAsync(s->row_type, rt.data(), ny, cudaMemcpyHostToDevice, s->stream), "row mask");
+    chk(cudaMemcpyAsync(s->col_type, ct.data(), s->col_bytes, cudaMemcpyHostToDevice, s->stream), "column mask");
+    chk(cudaMemsetAsync(s->buf[0], 0, s->buf_bytes, s->stream), "memset");
+    chk(cudaMemsetAsync(s->buf[1], 0, s->buf_bytes, s->stream), "memset");
+    chk(cudaMemsetAsync(s->obs, 0, s->L.total * sizeof(double), s->stream), "memset");
+    const double rho_slope = (drive == CLB_DRIVE_PRESSURE) ? (s->rho_out - s->rho_in) / (double)(nx - 1) : 0.0;
+    if (s->storage == CLB_FP64)
+        chk(launch_init<double>(s, s->buf[0], s->rho_in, rho_slope), "init");
+    else
+        chk(launch_init<float>(s, s->buf[0], s->rho_in, rho_slope), "init");
+    chk(cudaStreamSynchronize(s->stream), "sync");
+    if (st != CLB_OK) {
+        clb_destroy(s);
+        return st;
+    }
+    *out = s;
+    return CLB_OK;
+}
+
+clb_status clb_step(clb_sim* s, int64_t n) {
+    if (!s) return fail(CLB_EINVAL, "clb_step: sim is NULL");
+    if (n < 0) return fail(CLB_EINVAL, "clb_step: n < 0");
+    const int mode = s->drive == CLB_DRIVE_PRESSURE ? MODE_PRESSURE : MODE_PERIODIC;
+    SweepArgs a = make_args(s);
+    for (int64_t t = 0; t < n; ++t) {
+        a.fin = s->buf[s->cur];
+        a.fout = s->buf[s->cur ^ 1];
+        cudaError_t e = launch_sweep(s->storage, mode, s->vec, s->block_x, a, s->stream);
+        if (e != cudaSuccess) return fail(CLB_ECUDA, "clb_step: sweep launch: %s", cudaGetErrorString(e));
+        s->cur ^= 1;
+        ++s->step;
+    }
+    return CLB_OK;
+}
+
+clb_status clb_sync(clb_sim* s) {
+    if (!s) return fail(CLB_EINVAL, "clb_sync: sim is NULL");
+    CUDA_OR(cudaStreamSynchronize(s->stream));
+    return CLB_OK;
+}
+
+clb_status clb_info(const clb_sim* s, clb_info_t* info) {
+    if (!s || !info) return fail(CLB_EINVAL, "clb_info: NULL argument");
+    info->nx = s->nx;
+    info->ny = s->ny;
+    info->pitch = s->pitch;
+    info->storage = s->storage;
+    info->vec = s->vec;
+    info->block_x = s->block_x;
+    info->drive = s->drive;
+    info->bytes_per_node = 18.0 * (double)s->elem;
+    info->sv = s->sv;
+    info->sq = s->sq;
+    info->r = s->r;
+    info->kn = s->kn;
+    info->a = s->a;
+    info->g = s->g;
+    info->rho_in = s->rho_in;
+    info->rho_out = s->rho_out;
+    info->step = s->step;
+    info->stream = s->stream;
+    return CLB_OK;
+}
+
+clb_status clb_get_state(clb_sim* s, double* host_f) {
+    if (!s || !host_f) return fail(CLB_EINVAL, "clb_get_state: NULL argument");
+    const long long n = 9LL * s->nx * s->ny;
+    double* tmp = static_cast<double*>(s->dalloc(n * sizeof(double)));
+    if (!tmp) return fail(CLB_ENOMEM, "clb_get_state: device allocation failed");
+    clb_status st = CLB_OK;
+    if (s->storage == CLB_FP64)
+        to_canonical_kernel<double><<<grid_for(n, 256), 256, 0, s->stream>>>(
+            static_cast<const double*>(s->buf[s->cur]), tmp, s->nx, s->ny, s->pitch, s->xoff, s->plane, s->ref0,
+            s->ref_slope);
+    else
+        to_canonical_kernel<float><<<grid_for(n, 256), 256, 0, s->stream>>>(
+            static_cast<const float*>(s->buf[s->cur]), tmp, s->nx, s->ny, s->pitch, s->xoff, s->plane, s->ref0,
+            s->ref_slope);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_f, tmp, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) st = fail(CLB_ECUDA, "clb_get_state: %s", cudaGetErrorString(e));
+    s->dfree(tmp);
+    return st;
+}
+
+clb_status clb_set_state(clb_sim* s, const double* host_f) {
+    if (!s || !host_f) return fail(CLB_EINVAL, "clb_set_state: NULL argument");
+    const long long n = 9LL * s->nx * s->ny;
+    double* tmp = static_cast<double*>(s->dalloc(n * sizeof(double)));
+    if (!tmp) return fail(CLB_ENOMEM, "clb_set_state: device allocation failed");
+    clb_status st = CLB_OK;
+    cudaError_t e = cudaMemcpyAsync(tmp, host_f, n * sizeof(double), cudaMemcpyHostToDevice, s->stream);
+    const int periodic = s->drive == CLB_DRIVE_BODY_FORCE;
+    if (e == cudaSuccess) {
+        if (s->storage == CLB_FP64)
+            from_canonical_kernel<double><<<grid_for(n, 256), 256, 0, s->stream>>>(
+                tmp, static_cast<double*>(s->buf[s->cur]), s->nx, s->ny, s->pitch, s->xoff, s->plane, s->ref0,
+                s->ref_slope, periodic);
+        else
+            from_canonical_kernel<float><<<grid_for(n, 256), 256, 0, s->stream>>>(
+                tmp, static_cast<float*>(s->buf[s->cur]), s->nx, s->ny, s->pitch, s->xoff, s->plane, s->ref0,
+                s->ref_slope, periodic);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) st = fail(CLB_ECUDA, "clb_set_state: %s", cudaGetErrorString(e));
+    s->dfree(tmp);
+    s->have_prev = false;
+    return st;
+}
+
+clb_status clb_observables(clb_sim* s, int profile_col, clb_scalars* sc, double* ux_prof, double* uy_prof,
+                           double* p_centre, double* dp_nonlin, double* m_of_x) {
+    if (!s) return fail(CLB_EINVAL, "clb_observables: sim is NULL");
+    const int nx = s->nx, ny = s->ny;
+    if (profile_col < 0 || profile_col >= nx) profile_col = (s->drive == CLB_DRIVE_PRESSURE) ? nx - 1 : 0;
+    const double gx = s->drive == CLB_DRIVE_BODY_FORCE ? s->g : 0.0;
+    dim3 block(kObsCols, kObsRows);
+    dim3 grid(s->L.nblocks);
+    if (s->storage == CLB_FP64)
+        obs_kernel<double><<<grid, block, 0, s->stream>>>(static_cast<const double*>(s->buf[s->cur]), s->obs, s->L,
+                                                         nx, ny, s->pitch, s->xoff, s->plane, s->ref0, s->ref_slope,
+                                                         gx, 0.0, profile_col);
+    else
+        obs_kernel<float><<<grid, block, 0, s->stream>>>(static_cast<const float*>(s->buf[s->cur]), s->obs, s->L, nx,
+                                                        ny, s->pitch, s->xoff, s->plane, s->ref0, s->ref_slope, gx,
+                                                        0.0, profile_col);
+    CUDA_OR(cudaGetLastError());
+    obs_final_kernel<<<1, 32, 0, s->stream>>>(s->obs, s->L);
+    CUDA_OR(cudaGetLastError());
+    std::vector<double> h(s->L.part + 4);
+    CUDA_OR(cudaMemcpyAsync(h.data(), s->obs, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    CUDA_OR(cudaStreamSynchronize(s->stream));
+
+    const double* hm = h.data() + s->L.m;
+    const double* hrc = h.data() + s->L.rc;
+    const double* hux = h.data() + s->L.prof_x;
+    const double* huy = h.data() + s->L.prof_y;
+    const double msum = h[s->L.part + 0], usum = h[s->L.part + 1], mass = h[s->L.part + 2];
+    const double nbad = h[s->L.part + 3];
+    const double p_in = s->rho_in / 3.0, p_out = s->rho_out / 3.0;
+    const double L = nx > 1 ? (double)(nx - 1) : 1.0;
+    for (int x = 0; x < nx; ++x) {
+        const double pc = hrc[x] / 3.0;
+        if (p_centre) p_centre[x] = pc;
+        if (dp_nonlin) dp_nonlin[x] = (pc - (p_in - (p_in - p_out) * x / L)) / p_out;
+        if (m_of_x) m_of_x[x] = hm[x];
+    }
+    double umax = -INFINITY;
+    for (int y = 0; y < ny; ++y) {
+        if (ux_prof) ux_prof[y] = hux[y];
+        if (uy_prof) uy_prof[y] = huy[y];
+        umax = std::max(umax, hux[y]);
+    }
+    if (sc) {
+        const double mbar = msum / nx;
+        sc->mass_flow = mbar;
+        if (ny >= 2)
+            sc->u_slip = 0.5 * ((1.5 * hux[0] - 0.5 * hux[1]) + (1.5 * hux[ny - 1] - 0.5 * hux[ny - 2]));
+        else
+            sc->u_slip = hux[0];
+        if (s->drive == CLB_DRIVE_BODY_FORCE) {
+            // Q = sum_y u / (F H^2 sqrt(RT/2)/p) with RT = 1/3, p = rho0 RT, F = rho0 G
+            sc->q_norm = s->g != 0 ? (usum / nx) / (3.0 * s->g * (double)ny * ny * std::sqrt(1.0 / 6.0)) : 0.0;
+        } else {
+            // m_ns = H^3 (p_in^2 - p_out^2)/(24 mu RT L), mu = rho_out sqrt(6/pi) Kn_out N/3
+            const double mu = s->rho_out * std::sqrt(6.0 / kPi) * s->kn * ny / 3.0;
+            const double mns = (double)ny * ny * ny * (p_in * p_in - p_out * p_out) / (24.0 * mu * (1.0 / 3.0) * L);
+            sc->q_norm = mbar / mns;
+        }
+        sc->residual = s->have_prev && mbar != 0 ? std::fabs(mbar - s->prev_mass_flow) / std::fabs(mbar) : -1.0;
+        sc->total_mass = mass;
+        sc->ux_max = umax;
+        sc->step = s->step;
+        s->prev_mass_flow = mbar;
+        s->have_prev = true;
+    }
+    if (nbad > 0) return fail(CLB_ENUMERIC, "clb_observables: %.0f nodes with a non-finite density or velocity", nbad);
+    return CLB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,376 @@
+// Fused D2Q9 stream-and-collide sweep of the cascaded lattice Boltzmann (CLB)
+// channel solver (Liu & He, arXiv:1603.01955), hand-written for GB300 (sm_103a).
+//
+// One launch = one time step for every node: pull-streaming of the
+// post-collision populations of the last step (Eq. 5), CBBSR walls in the
+// first and last rows (Eq. 20 and its mirror), pressure inlet/outlet columns
+// (Sec. 3.2) or periodic x (Sec. 3.1), then the cascaded collision (Eq. 4,
+// 6-13) with per-node relaxation rates (Eq. 18, 21), stored into the other
+// buffer.
+//
+// Layout: structure of arrays, plane i (direction e_i of Eq. 1) of ny rows,
+// each row `pitch` elements with column x at element xoff + x (xoff = 128
+// bytes), so that every row and every vector of V columns is aligned.  Column
+// -1 and column nx are halo columns that the previous sweep filled with the
+// periodic images, so no wrap-around appears in the loads.
+//
+// Launch: one row per blockIdx.y, V consecutive nodes per thread along x.  A
+// thread loads each plane as one 8/16-byte vector; the populations that move
+// along x arrive from the neighbouring lane by a warp shuffle, and only lanes 0
+// and 31 load the one element across the warp edge.  The wall rows are whole
+// blocks, so the wall branch never diverges inside a warp.  Boundary nodes of
+// a pressure channel are found through the column-type mask and rebuilt before
+// their collision.  No value is read twice from DRAM: every population of the
+// last step is pulled by exactly one node.
+#include <cstdint>
+#include <type_traits>
+
+#include "clb_device.cuh"
+#include "clb_internal.h"
+
+namespace clb {
+
+template <class T, int V> struct Vec;
+template <> struct Vec<float, 1> { using type = float; };
+template <> struct Vec<float, 2> { using type = float2; };
+template <> struct Vec<float, 4> { using type = float4; };
+template <> struct Vec<double, 1> { using type = double; };
+template <> struct Vec<double, 2> { using type = double2; };
+
+template <class T, int V>
+__device__ __forceinline__ void vload(const T* p, T (&v)[V]) {
+    using VT = typename Vec<T, V>::type;
+    const VT w = __ldg(reinterpret_cast<const VT*>(p));
+    const T* e = reinterpret_cast<const T*>(&w);
+#pragma unroll
+    for (int k = 0; k < V; ++k) v[k] = e[k];
+}
+
+template <class T, int V>
+__device__ __forceinline__ void vstore(T* p, const T (&v)[V]) {
+    using VT = typename Vec<T, V>::type;
+    VT w;
+    T* e = reinterpret_cast<T*>(&w);
+#pragma unroll
+    for (int k = 0; k < V; ++k) e[k] = v[k];
+    *reinterpret_cast<VT*>(p) = w;
+}
+
+// V columns x0..x0+V-1 of one row (zeros for threads past the halo column).
+template <class T, class R, int V>
+__device__ __forceinline__ void row_vec(const T* row, int x0, bool live, R (&o)[V]) {
+    T v[V];
+    if (live) {
+        vload<T, V>(row + x0, v);
+    } else {
+#pragma unroll
+        for (int k = 0; k < V; ++k) v[k] = T(0);
+    }
+#pragma unroll
+    for (int k = 0; k < V; ++k) o[k] = R(v[k]);
+}
+
+// Columns x0-1..x0+V-2 from the vector of columns x0..x0+V-1 (a population
+// moving in +x): the first element comes from the previous lane.
+template <class T, class R, int V>
+__device__ __forceinline__ void from_left(const R (&v)[V], const T* row, int x0, int lane, R (&o)[V]) {
+    R prev = __shfl_up_sync(0xffffffffu, v[V - 1], 1);
+    if (lane == 0) prev = R(__ldg(row + x0 - 1));
+    o[0] = prev;
+#pragma unroll
+    for (int k = 1; k < V; ++k) o[k] = v[k - 1];
+}
+
+// Columns x0+1..x0+V (a population moving in -x): the last element comes from
+// the next lane.
+template <class T, class R, int V>
+__device__ __forceinline__ void from_right(const R (&v)[V], const T* row, int x0, int lane, bool live,
+                                           R (&o)[V]) {
+    R next = __shfl_down_sync(0xffffffffu, v[0], 1);
+    if (lane == 31 && live) next = R(__ldg(row + x0 + V));
+#pragma unroll
+    for (int k = 0; k < V - 1; ++k) o[k] = v[k + 1];
+    o[V - 1] = next;
+}
+
+template <class R, int V>
+__device__ __forceinline__ void add_shift(R (&o)[V], R s) {
+#pragma unroll
+    for (int k = 0; k < V; ++k) o[k] += s;
+}
+
+// Pre-collision deviations at one interior node (x in 1..nx-2) of a pressure
+// channel, gathered element by element; used only to rebuild the end columns.
+template <class T, class R>
+__device__ void gather_node(const SweepArgs& a, const KC<R>& c, const T* fin, int x, int y, R o[9]) {
+    const long long P = a.plane;
+    const T* row = fin + (long long)y * a.pitch + a.xoff;
+    auto at = [&](int i, int dy, int xx) -> R { return R(__ldg(row + i * P + (long long)dy * a.pitch + xx)); };
+    const int rt = a.row_type[y];
+    const R sha = c.sha, shd = c.shd;  // source at x-1; the source at x+1 gets the negative
+    o[0] = at(0, 0, x);
+    o[1] = at(1, 0, x - 1) + sha;
+    o[3] = at(3, 0, x + 1) - sha;
+    if (rt & ROW_BOTTOM) {
+        o[2] = at(4, 0, x);
+        o[5] = c.r * at(7, 0, x) + c.rc * (at(8, 0, x - 1) + shd);
+        o[6] = c.r * at(8, 0, x) + c.rc * (at(7, 0, x + 1) - shd);
+    } else {
+        o[2] = at(2, -1, x);
+        o[5] = at(5, -1, x - 1) + shd;
+        o[6] = at(6, -1, x + 1) - shd;
+    }
+    if (rt & ROW_TOP) {
+        o[4] = at(2, 0, x);
+        o[7] = c.r * at(5, 0, x) + c.rc * (at(6, 0, x + 1) - shd);
+        o[8] = c.r * at(6, 0, x) + c.rc * (at(5, 0, x - 1) + shd);
+    } else {
+        o[4] = at(4, 1, x);
+        o[7] = at(7, 1, x + 1) - shd;
+        o[8] = at(8, 1, x - 1) + shd;
+    }
+}
+
+// Pressure column rebuilt by linear extrapolation (reading of Sec. 3.2):
+//   f_i(b) = f^eq_i(rho_b, u_b) + f^neq_i(b+d),  u_b = 2 u(b+d) - u(b+2d),
+//   f^neq = f - f^eq(rho, u),
+// with d = +1 at the inlet (rho_b = rho_in) and -1 at the outlet (rho_out):
+// the velocity is extrapolated linearly, the non-equilibrium part comes from
+// the first interior neighbour (a linear extrapolation of it as well would
+// amplify the shortest x-wavelength threefold and diverge at tau ~ 30).
+// Output: deviations relative to R(b).
+template <class T, class R>
+__device__ __forceinline__ void rebuild_column(const SweepArgs& a, const KC<R>& c, const T* fin, int x, int y,
+                                            bool inlet, R* out) {
+    const int dir = inlet ? 1 : -1;
+    R n1[9], n2[9], e1[9], eb[9];
+    gather_node<T, R>(a, c, fin, x + dir, y, n1);
+    gather_node<T, R>(a, c, fin, x + 2 * dir, y, n2);
+    R dr1, jx1, jy1, dr2, jx2, jy2;
+    macro_dev(n1, dr1, jx1, jy1);
+    macro_dev(n2, dr2, jx2, jy2);
+    const R r1 = c.ref0 + c.slope * R(x + dir) + dr1;
+    const R r2 = c.ref0 + c.slope * R(x + 2 * dir) + dr2;
+    const R u1x = jx1 / r1, u1y = jy1 / r1, u2x = jx2 / r2, u2y = jy2 / r2;
+    feq_dev(dr1, r1, u1x, u1y, e1);
+    const R drb = inlet ? c.drho_in : c.drho_out;
+    const R rb = c.ref0 + c.slope * R(x) + drb;
+    feq_dev(drb, rb, R(2) * u1x - u2x, R(2) * u1y - u2y, eb);
+    // the neighbour's deviations are relative to R(x+d); f^neq does not depend
+    // on the reference, so only the equilibrium carries R(b)
+#pragma unroll
+    for (int i = 0; i < 9; ++i) out[i] = eb[i] + (n1[i] - e1[i]);
+}
+
+template <class T, int MODE, int V>
+__global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a) {
+    using R = typename std::conditional<std::is_same<T, double>::value, double, float>::type;
+    constexpr bool kShift = (MODE == MODE_PRESSURE) && !std::is_same<T, double>::value;
+    const T* __restrict__ fin = static_cast<const T*>(a.fin);
+    T* __restrict__ fout = static_cast<T*>(a.fout);
+
+    const int lane = threadIdx.x & 31;
+    const int y = blockIdx.y;
+    const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * V;
+    if (x0 - lane * V > a.nx) return;  // the whole warp lies past the halo column
+    const bool live = x0 <= a.nx;      // this thread's vector can feed a real node
+
+    KC<R> c;
+    c.load(a);
+    const long long P = a.plane;
+    const T* row = fin + (long long)y * a.pitch + a.xoff;  // plane 0, row y, column 0
+    const int rt = a.row_type[y];
+
+    R f[9][V];
+    // rest population and the two that move along x only (Eq. 5)
+    row_vec<T, R, V>(row, x0, live, f[0]);
+    {
+        R v[V];
+        row_vec<T, R, V>(row + 1 * P, x0, live, v);
+        from_left<T, R, V>(v, row + 1 * P, x0, lane, f[1]);
+        row_vec<T, R, V>(row + 3 * P, x0, live, v);
+        from_right<T, R, V>(v, row + 3 * P, x0, lane, live, f[3]);
+        if (kShift) {
+            add_shift<R, V>(f[1], c.sha);
+            add_shift<R, V>(f[3], -c.sha);
+        }
+    }
+    // populations entering from the row below: 2, 5, 6
+    if (rt & ROW_BOTTOM) {
+        // Eq. 20: fbar2 = f~4, fbar5 = r f~7 + (1-r) f~8(x-1), fbar6 = r f~8 + (1-r) f~7(x+1)
+        R v4[V], v7[V], v8[V], s8[V], s7[V];
+        row_vec<T, R, V>(row + 4 * P, x0, live, v4);
+        row_vec<T, R, V>(row + 7 * P, x0, live, v7);
+        row_vec<T, R, V>(row + 8 * P, x0, live, v8);
+        from_left<T, R, V>(v8, row + 8 * P, x0, lane, s8);
+        from_right<T, R, V>(v7, row + 7 * P, x0, lane, live, s7);
+        if (kShift) {
+            add_shift<R, V>(s8, c.shd);
+            add_shift<R, V>(s7, -c.shd);
+        }
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            f[2][k] = v4[k];
+            f[5][k] = c.r * v7[k] + c.rc * s8[k];
+            f[6][k] = c.r * v8[k] + c.rc * s7[k];
+        }
+    } else {
+        const T* rd = row - a.pitch;
+        R v[V];
+        row_vec<T, R, V>(rd + 2 * P, x0, live, f[2]);
+        row_vec<T, R, V>(rd + 5 * P, x0, live, v);
+        from_left<T, R, V>(v, rd + 5 * P, x0, lane, f[5]);
+        row_vec<T, R, V>(rd + 6 * P, x0, live, v);
+        from_right<T, R, V>(v, rd + 6 * P, x0, lane, live, f[6]);
+        if (kShift) {
+            add_shift<R, V>(f[5], c.shd);
+            add_shift<R, V>(f[6], -c.shd);
+        }
+    }
+    // populations entering from the row above: 4, 7, 8
+    if (rt & ROW_TOP) {
+        // mirror of Eq. 20: fbar4 = f~2, fbar7 = r f~5 + (1-r) f~6(x+1), fbar8 = r f~6 + (1-r) f~5(x-1)
+        R v2[V], v5[V], v6[V], s6[V], s5[V];
+        row_vec<T, R, V>(row + 2 * P, x0, live, v2);
+        row_vec<T, R, V>(row + 5 * P, x0, live, v5);
+        row_vec<T, R, V>(row + 6 * P, x0, live, v6);
+        from_right<T, R, V>(v6, row + 6 * P, x0, lane, live, s6);
+        from_left<T, R, V>(v5, row + 5 * P, x0, lane, s5);
+        if (kShift) {
+            add_shift<R, V>(s6, -c.shd);
+            add_shift<R, V>(s5, c.shd);
+        }
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            f[4][k] = v2[k];
+            f[7][k] = c.r * v5[k] + c.rc * s6[k];
+            f[8][k] = c.r * v6[k] + c.rc * s5[k];
+        }
+    } else {
+        const T* ru = row + a.pitch;
+        R v[V];
+        row_vec<T, R, V>(ru + 4 * P, x0, live, f[4]);
+        row_vec<T, R, V>(ru + 7 * P, x0, live, v);
+        from_right<T, R, V>(v, ru + 7 * P, x0, lane, live, f[7]);
+        row_vec<T, R, V>(ru + 8 * P, x0, live, v);
+        from_left<T, R, V>(v, ru + 8 * P, x0, lane, f[8]);
+        if (kShift) {
+            add_shift<R, V>(f[7], -c.shd);
+            add_shift<R, V>(f[8], c.shd);
+        }
+    }
+    if (!live || x0 >= a.nx) return;  // nothing of this thread's own to store
+
+    // node-type mask of this thread's columns: at most one inlet and one
+    // outlet node, rebuilt here (Sec. 3.2) before the collision loop
+    uint8_t ct[V];
+    int kin = -1, kout = -1;
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+        ct[k] = a.col_type[x0 + k];
+        if (MODE == MODE_PRESSURE) {
+            if (ct[k] & COL_INLET) kin = k;
+            if (ct[k] & COL_OUTLET) kout = k;
+        }
+    }
+    if (MODE == MODE_PRESSURE) {
+        if (kin >= 0) {
+            R t[9];
+            rebuild_column<T, R>(a, c, fin, x0 + kin, y, true, t);
+#pragma unroll
+            for (int k = 0; k < V; ++k)
+                if (k == kin)
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) f[i][k] = t[i];
+        }
+        if (kout >= 0) {
+            R t[9];
+            rebuild_column<T, R>(a, c, fin, x0 + kout, y, false, t);
+#pragma unroll
+            for (int k = 0; k < V; ++k)
+                if (k == kout)
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) f[i][k] = t[i];
+        }
+    }
+
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+        R d[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) d[i] = f[i][k];
+        const R ref = (MODE == MODE_PRESSURE) ? c.ref0 + c.slope * R(x0 + k) : c.ref0;
+        collide<R, MODE>(d, ref, c);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f[i][k] = d[i];
+    }
+
+    T* orow = fout + (long long)y * a.pitch + a.xoff;
+    if (x0 + V <= a.nx) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            T v[V];
+#pragma unroll
+            for (int k = 0; k < V; ++k) v[k] = T(f[i][k]);
+            vstore<T, V>(orow + i * P + x0, v);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < V; ++k)
+            if (x0 + k < a.nx)
+#pragma unroll
+                for (int i = 0; i < 9; ++i) orow[i * P + x0 + k] = T(f[i][k]);
+    }
+    if (MODE == MODE_PERIODIC) {
+        // periodic images for the next sweep: column 0 -> halo column nx
+        // (populations moving in -x), column nx-1 -> halo column -1 (moving in +x)
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            if (ct[k] & COL_HALO_RIGHT) {
+                orow[3 * P + a.nx] = T(f[3][k]);
+                orow[6 * P + a.nx] = T(f[6][k]);
+                orow[7 * P + a.nx] = T(f[7][k]);
+            }
+            if (ct[k] & COL_HALO_LEFT) {
+                orow[1 * P - 1] = T(f[1][k]);
+                orow[5 * P - 1] = T(f[5][k]);
+                orow[8 * P - 1] = T(f[8][k]);
+            }
+        }
+    }
+}
+
+template <class T, int MODE, int V>
+static cudaError_t launch_one(int block_x, const SweepArgs& a, cudaStream_t s) {
+    const int groups = (a.nx + V) / V;  // vectors covering columns 0..nx (halo included)
+    dim3 block(block_x, 1, 1);
+    dim3 grid((groups + block_x - 1) / block_x, a.ny, 1);
+    sweep_kernel<T, MODE, V><<<grid, block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <class T, int V>
+static cudaError_t launch_mode(int mode, int block_x, const SweepArgs& a, cudaStream_t s) {
+    if (mode == MODE_PRESSURE) return launch_one<T, MODE_PRESSURE, V>(block_x, a, s);
+    return launch_one<T, MODE_PERIODIC, V>(block_x, a, s);
+}
+
+bool sweep_supported(int storage, int vec) {
+    if (storage == 0) return vec == 1 || vec == 2;
+    if (storage == 1) return vec == 1 || vec == 2 || vec == 4;
+    return false;
+}
+
+cudaError_t launch_sweep(int storage, int mode, int vec, int block_x, const SweepArgs& a, cudaStream_t s) {
+    if (storage == 0) {
+        if (vec == 1) return launch_mode<double, 1>(mode, block_x, a, s);
+        if (vec == 2) return launch_mode<double, 2>(mode, block_x, a, s);
+    } else if (storage == 1) {
+        if (vec == 1) return launch_mode<float, 1>(mode, block_x, a, s);
+        if (vec == 2) return launch_mode<float, 2>(mode, block_x, a, s);
+        if (vec == 4) return launch_mode<float, 4>(mode, block_x, a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace clb
