@@ -71,7 +71,7 @@ typedef struct {
     double rho_out; /* outlet density (pressure drive) or mean density (body force); 1.0 */
     int storage;    /* clb_storage; CLB_FP32_SHIFTED */
     int vec;        /* nodes per thread along x (1, 2 or 4 for FP32, 1 or 2 for FP64); 0 = default */
-    int block_x;    /* threads per block (multiple of 32, <= 1024); 0 = default 128 */
+    int block_x;    /* threads per block, a multiple of 32 in 32..256; 0 = default 128 */
     void* stream;   /* cudaStream_t to queue work on; NULL = a stream owned by the library */
     /* Device allocator hooks (e.g. a framework's caching allocator); both NULL
      * = cudaMalloc / cudaFree.  alloc returns NULL on failure. */
@@ -170,6 +170,7 @@ clb_status clb_destroy(clb_sim* sim);
 
 /* Message for the last failing call on this thread ("" if none). */
 const char* clb_last_error(void);
+
 
 #ifdef __cplusplus
 }

@@ -16,6 +16,21 @@ enum : uint8_t { ROW_BOTTOM = 1, ROW_TOP = 2 };
 // the halo columns -1 and nx so that the next sweep needs no wrap-around.
 enum : uint8_t { COL_INLET = 1, COL_OUTLET = 2, COL_HALO_RIGHT = 4, COL_HALO_LEFT = 8 };
 
+// Launch constants in the compute type of a sweep, derived on the host so
+// that no thread spends FP64 instructions on them (GB300's FP64 rate is a
+// small fraction of its FP32 rate).
+template <typename R> struct KC {
+    R s3_12, s8_4;    // s3/12, s8/4
+    R sv_4, sq_4;     // constant s_v/4, s_q/4 (body-force channel)
+    R A, B, A316, CA; // pressure channel: tau = A/(rho+B); 3/(16A); (pi B2/4) A
+    R hfx, hfy;       // F/2
+    R fx, fy;         // F
+    R r, rc;          // r_b, 1 - r_b
+    R ref0, slope;    // deviation reference R(x) = ref0 + slope x
+    R sha, shd;       // added to a value pulled from column x-1: -w slope (axis, diagonal)
+    R drho_in, drho_out;
+};
+
 // Everything one sweep launch needs (passed by value as a kernel argument).
 struct SweepArgs {
     const void* fin;          // populations of the last step (post-collision)
@@ -37,7 +52,12 @@ struct SweepArgs {
     // R(x) = ref0 + ref_slope * x (R = 0 for FP64 storage).
     double ref0, ref_slope;
     double drho_in, drho_out; // rho_in - R(0), rho_out - R(nx-1)
+    KC<float> kf;             // the constants above, derived, in FP32
+    KC<double> kd;            // ... and in FP64
 };
+
+// Fill a.kf and a.kd from the double fields of a.
+void derive_constants(SweepArgs& a);
 
 // Launch one sweep.  storage: clb_storage value; mode: MODE_*; vec: nodes per
 // thread along x; block_x: threads per block.

@@ -298,6 +298,7 @@ SweepArgs make_args(const clb_sim* s) {
     a.ref_slope = s->ref_slope;
     a.drho_in = s->rho_in - s->ref_at(0);
     a.drho_out = s->rho_out - s->ref_at(s->nx - 1);
+    derive_constants(a);
     return a;
 }
 
@@ -650,3 +651,4 @@ clb_status clb_observables(clb_sim* s, int profile_col, clb_scalars* sc, double*
 }
 
 }  // extern "C"
+

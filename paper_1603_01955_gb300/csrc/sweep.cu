@@ -175,8 +175,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a) {
     if (x0 - lane * V > a.nx) return;  // the whole warp lies past the halo column
     const bool live = x0 <= a.nx;      // this thread's vector can feed a real node
 
-    KC<R> c;
-    c.load(a);
+    const KC<R>& c = kc<R>(a);
     const long long P = a.plane;
     const T* row = fin + (long long)y * a.pitch + a.xoff;  // plane 0, row y, column 0
     const int rt = a.row_type[y];
@@ -353,6 +352,34 @@ template <class T, int V>
 static cudaError_t launch_mode(int mode, int block_x, const SweepArgs& a, cudaStream_t s) {
     if (mode == MODE_PRESSURE) return launch_one<T, MODE_PRESSURE, V>(block_x, a, s);
     return launch_one<T, MODE_PERIODIC, V>(block_x, a, s);
+}
+
+template <typename R> static void fill(KC<R>& c, const SweepArgs& a) {
+    c.s3_12 = R(a.s3 / 12.0);
+    c.s8_4 = R(a.s8 / 4.0);
+    c.sv_4 = R(a.sv / 4.0);
+    c.sq_4 = R(a.sq / 4.0);
+    c.A = R(a.rate_A);
+    c.B = R(a.rate_B);
+    c.A316 = a.rate_A > 0 ? R(3.0 / (16.0 * a.rate_A)) : R(0);
+    c.CA = R(a.rate_C * a.rate_A);
+    c.hfx = R(0.5 * a.gx);
+    c.hfy = R(0.5 * a.gy);
+    c.fx = R(a.gx);
+    c.fy = R(a.gy);
+    c.r = R(a.r);
+    c.rc = R(1.0 - a.r);
+    c.ref0 = R(a.ref0);
+    c.slope = R(a.ref_slope);
+    c.sha = R(-a.ref_slope / 9.0);
+    c.shd = R(-a.ref_slope / 36.0);
+    c.drho_in = R(a.drho_in);
+    c.drho_out = R(a.drho_out);
+}
+
+void derive_constants(SweepArgs& a) {
+    fill(a.kf, a);
+    fill(a.kd, a);
 }
 
 bool sweep_supported(int storage, int vec) {

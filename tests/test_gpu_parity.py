@@ -5,11 +5,13 @@ Tolerances:
 * FP64 storage: 1e-12 relative per population after 1000 steps (the target
   stated for the plain FP64 path); both sides evaluate the same formulas in
   FP64 in different orders, so only round-off separates them.
-* FP32-shifted storage: the stored deviations d = f - w R carry a relative
-  rounding of 2^-24 per step; with |d| <= D the per-population error after n
-  steps stays below c * 2^-24 * D * sqrt(n) for a small c.  The bound used is
-  TOL32 * max|d| with TOL32 = 2e-6 (c ~ 1 at n = 1000), and the mass flow
-  within 1e-5 relative (the target stated for this path).
+* FP32-shifted storage: the stored values are deviations d = f - w_i R(x) from
+  the reference density R (the linear initial profile of a pressure channel,
+  rho_out otherwise).  Each step rounds them once on store and the collision
+  adds a few FP32 roundings on quantities no larger than max|d|; over n steps
+  of a non-amplifying update these add up like a random walk, so the bound is
+  c * 2^-24 * sqrt(n) * max|d| per population with c = 4 (observed c ~ 2),
+  and the mass flow within 1e-5 relative (the target stated for this path).
 """
 import numpy as np
 import pytest
@@ -19,7 +21,16 @@ import inputs
 pytestmark = pytest.mark.gpu
 
 TOL64 = 1e-12
-TOL32 = 2e-6
+
+
+def tol32(n):
+    return 4 * 2.0**-24 * np.sqrt(max(n, 1))
+
+
+def rho_bound(n, scale):
+    """Largest density error of a node implied by the per-population bound
+    (a density is the sum of nine populations)."""
+    return 9 * tol32(n) * scale
 
 
 @pytest.fixture(scope="module")
@@ -55,11 +66,16 @@ def per_pop_rel(got, want):
     return (np.abs(got - want) / np.abs(want)).max()
 
 
-def dev_scale(orc_state, oracle_mod):
-    """max |f - w rho_ref| of an oracle state (the size of FP32-stored deviations)."""
+def dev_scale(orc_state, oracle_mod, drive, ratio=1.0):
+    """max |f - w_i R(x)| of an oracle state: the size of the FP32-stored
+    deviations (R linear from ratio to 1 in a pressure channel, 1 otherwise)."""
+    nx = orc_state.shape[2]
     w = oracle_mod.feq(1.0, 0.0, 0.0)[:, None, None]
-    rho = orc_state.sum(axis=0)[None]
-    return np.abs(orc_state - w * rho).max() + 1e-30
+    if drive == "pressure":
+        R = ratio + (1.0 - ratio) * np.arange(nx) / (nx - 1)
+    else:
+        R = np.ones(nx)
+    return np.abs(orc_state - w * R[None, None, :]).max() + 1e-30
 
 
 # ------------------------------------------------------------- FP64 parity
@@ -179,7 +195,7 @@ def test_fp32_periodic_channel_4x32_1000_steps(clb, oracle_mod):
     ch.step(1000)
     orc.step(1000)
     so = orc.state()
-    assert np.abs(ch.state() - so).max() <= TOL32 * dev_scale(so, oracle_mod)
+    assert np.abs(ch.state() - so).max() <= tol32(1000) * dev_scale(so, oracle_mod, "body_force")
     assert ch.observables()["mass_flow"] == pytest.approx(orc.observables()["mass_flow"], rel=1e-5)
 
 
@@ -190,10 +206,12 @@ def test_fp32_pressure_channel_1601x16_1000_steps(clb, oracle_mod, kn_out):
     ch.step(1000)
     orc.step(1000)
     so = orc.state()
-    assert np.abs(ch.state() - so).max() <= TOL32 * dev_scale(so, oracle_mod)
     g, o = ch.observables(), orc.observables()
+    scale = dev_scale(so, oracle_mod, "pressure", c["ratio"])
+    assert np.abs(ch.state() - so).max() <= tol32(1000) * scale
     assert g["mass_flow"] == pytest.approx(o["mass_flow"], rel=1e-5)
-    assert np.abs(g["dp_nonlin"] - o["dp_nonlin"]).max() <= 1e-5 * np.abs(o["dp_nonlin"]).max() + 1e-7
+    # dp = (rho_c/3 - p_l)/p_out with p_out = 1/3: its error is the density error
+    assert np.abs(g["dp_nonlin"] - o["dp_nonlin"]).max() <= rho_bound(1000, scale)
 
 
 @pytest.mark.parametrize("nx,ny,drive,vec,block_x", EDGE)
@@ -208,7 +226,7 @@ def test_fp32_edge_sizes_and_launch_shapes(clb, oracle_mod, nx, ny, drive, vec, 
         ch.step(150)
         orc.step(150)
         so = orc.state()
-        assert np.abs(ch.state() - so).max() <= TOL32 * np.abs(so).max()
+        assert np.abs(ch.state() - so).max() <= tol32(150) * dev_scale(so, oracle_mod, drive, value)
 
 
 @pytest.mark.parametrize("seed", inputs.SEEDS[:3])
@@ -225,4 +243,7 @@ def test_fp32_random_states(clb, oracle_mod, seed):
     ch.step(200)
     orc.step(200)
     so = orc.state()
-    assert np.abs(ch.state() - so).max() <= TOL32 * np.abs(so).max()
+    scale = dev_scale(so, oracle_mod, drive, value)
+    assert np.abs(ch.state() - so).max() <= tol32(200) * scale
+    nodes = nx * ny
+    assert abs(ch.observables()["total_mass"] - orc.observables()["total_mass"]) <= nodes * rho_bound(200, scale)
