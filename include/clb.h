@@ -171,6 +171,45 @@ clb_status clb_destroy(clb_sim* sim);
 /* Message for the last failing call on this thread ("" if none). */
 const char* clb_last_error(void);
 
+/*
+ * clb_observables_noalloc - the observables of clb_observables, computed from
+ * populations the caller already holds in device memory, without allocating
+ * anything.  The paper has no counterpart: this is a library convenience.
+ *
+ * Who needs it: callers that may not allocate device memory at the time they
+ * want the numbers - for instance a program whose device memory is owned by
+ * another runtime's allocator or fully budgeted in advance, where cudaMalloc
+ * could fail or would stall every stream of the device.  Such a caller passes
+ * its own input and output buffers; this call uses no cudaMalloc, cudaFree or
+ * allocating library routine, and no allocator hook.
+ *
+ *   f_dev        device pointer to FP64 post-collision populations [9][ny][nx],
+ *                index (i*ny + y)*nx + x (the layout of clb_get_state)
+ *   nx, ny       1 <= nx <= 65536, 1 <= ny <= 4096; larger sizes are rejected
+ *                with CLB_EINVAL and a message naming the limit
+ *   drive, g, rho_in, rho_out, kn
+ *                the problem statement needed by the scalars (as in clb_create:
+ *                g is the body force, kn the (outlet) Knudsen number)
+ *   profile_col  as in clb_observables
+ *   stream       cudaStream_t to run on (NULL = legacy default stream); the call
+ *                synchronises it before returning
+ *   outputs      host arrays as in clb_observables (each may be NULL);
+ *                s->residual and s->step are -1 (this call keeps no state)
+ *
+ * Scratch: a fixed device array of about 1.2 MB inside the library (enough for
+ * the maximum sizes above), which every GPU that loads the library holds until
+ * the process exits.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress) with the device current; make that first call
+ * before any stream capture.  All calls on a device share the array: calls that
+ * overlap on the GPU (from several streams or threads at once) race and give
+ * wrong results; serialise them.  The array keeps the last call's contents, and
+ * each call clears the part it uses before reducing.
+ * Errors: CLB_EINVAL, CLB_ECUDA, CLB_ENUMERIC (non-finite field, outputs written).
+ */
+clb_status clb_observables_noalloc(const double* f_dev, int nx, int ny, int drive, double g, double rho_in,
+                                   double rho_out, double kn, int profile_col, void* stream, clb_scalars* s,
+                                   double* ux_prof, double* uy_prof, double* p_centre, double* dp_nonlin,
+                                   double* m_of_x);
 
 #ifdef __cplusplus
 }

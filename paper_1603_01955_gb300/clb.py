@@ -88,8 +88,10 @@ def _load():
     lib.clb_destroy.argtypes = [P]
     lib.clb_last_error.argtypes = []
     lib.clb_last_error.restype = C.c_char_p
+    lib.clb_observables_noalloc.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
+                                            C.c_double, C.c_int, P, C.POINTER(clb_scalars), D, D, D, D, D]
     for name in ("clb_create", "clb_step", "clb_observables", "clb_get_state", "clb_set_state",
-                 "clb_info", "clb_sync", "clb_destroy"):
+                 "clb_info", "clb_sync", "clb_destroy", "clb_observables_noalloc"):
         getattr(lib, name).restype = C.c_int
     return lib
 
@@ -133,6 +135,16 @@ def clb_step(sim, n):
 def clb_observables(sim, profile_col, s, ux_prof, uy_prof, p_centre, dp_nonlin, m_of_x, check=True):
     st = lib.clb_observables(sim, int(profile_col), C.byref(s) if s is not None else None, _dptr(ux_prof),
                              _dptr(uy_prof), _dptr(p_centre), _dptr(dp_nonlin), _dptr(m_of_x))
+    return _check(st) if check else st
+
+
+def clb_observables_noalloc(f_dev_ptr, nx, ny, drive, g, rho_in, rho_out, kn, profile_col, stream_ptr, s,
+                            ux_prof, uy_prof, p_centre, dp_nonlin, m_of_x, check=True):
+    """Observables of a caller-owned FP64 device array [9][ny][nx]; allocates nothing."""
+    st = lib.clb_observables_noalloc(C.c_void_p(f_dev_ptr), int(nx), int(ny), int(drive), float(g), float(rho_in),
+                                     float(rho_out), float(kn), int(profile_col), C.c_void_p(stream_ptr),
+                                     C.byref(s) if s is not None else None, _dptr(ux_prof), _dptr(uy_prof),
+                                     _dptr(p_centre), _dptr(dp_nonlin), _dptr(m_of_x))
     return _check(st) if check else st
 
 

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -652,3 +653,116 @@ clb_status clb_observables(clb_sim* s, int profile_col, clb_scalars* sc, double*
 
 }  // extern "C"
 
+// ---------------------------------------------------- allocation-free variant
+//
+// clb_observables_noalloc: the observable reduction above, for callers that
+// hold the populations in device memory of their own and may not allocate any
+// (see include/clb.h).  Its scratch is a fixed array in this file, shared by
+// every call on a device and kept until the process exits.
+
+namespace {
+
+constexpr int kNoAllocMaxNx = 65536;
+constexpr int kNoAllocMaxNy = 4096;
+constexpr size_t kNoAllocScratch =
+    2 * (size_t)kNoAllocMaxNx + 2 * (size_t)kNoAllocMaxNy + 4 * (size_t)((kNoAllocMaxNx + kObsCols - 1) / kObsCols);
+constexpr int kNoAllocMaxDevices = 64;
+
+__device__ __align__(256) double g_noalloc_scratch[kNoAllocScratch];
+
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device, looked up once
+// per device (the name is only a host-side stand-in for it).
+clb_status noalloc_scratch(double** out) {
+    int dev = -1;
+    CUDA_OR(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(CLB_EINVAL, "clb_observables_noalloc: device %d", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(CLB_ECUDA, "clb_observables_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        g_noalloc_ptr[dev] = static_cast<double*>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return CLB_OK;
+}
+
+}  // namespace
+
+extern "C" clb_status clb_observables_noalloc(const double* f_dev, int nx, int ny, int drive, double g,
+                                              double rho_in, double rho_out, double kn, int profile_col,
+                                              void* stream, clb_scalars* sc, double* ux_prof, double* uy_prof,
+                                              double* p_centre, double* dp_nonlin, double* m_of_x) {
+    if (!f_dev) return fail(CLB_EINVAL, "clb_observables_noalloc: populations pointer is NULL");
+    if (nx < 1 || nx > kNoAllocMaxNx || ny < 1 || ny > kNoAllocMaxNy)
+        return fail(CLB_EINVAL, "clb_observables_noalloc: nx = %d, ny = %d outside 1..%d x 1..%d", nx, ny,
+                    kNoAllocMaxNx, kNoAllocMaxNy);
+    if (drive != CLB_DRIVE_BODY_FORCE && drive != CLB_DRIVE_PRESSURE)
+        return fail(CLB_EINVAL, "clb_observables_noalloc: unknown drive %d", drive);
+    if (drive == CLB_DRIVE_PRESSURE && !(kn > 0 && rho_in > 0 && rho_out > 0))
+        return fail(CLB_EINVAL, "clb_observables_noalloc: pressure drive needs kn, rho_in, rho_out > 0");
+    double* scratch = nullptr;
+    clb_status st = noalloc_scratch(&scratch);
+    if (st != CLB_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (profile_col < 0 || profile_col >= nx) profile_col = (drive == CLB_DRIVE_PRESSURE) ? nx - 1 : 0;
+    const ObsLayout L = obs_layout(nx, ny);
+    const double gx = drive == CLB_DRIVE_BODY_FORCE ? g : 0.0;
+    // the previous call's values stay in the array; start from zeros
+    CUDA_OR(cudaMemsetAsync(scratch, 0, L.total * sizeof(double), s));
+    // populations in the canonical layout: row pitch nx, no halo, plain FP64 (R = 0)
+    obs_kernel<double><<<dim3(L.nblocks), dim3(kObsCols, kObsRows), 0, s>>>(
+        f_dev, scratch, L, nx, ny, nx, 0, (long long)nx * ny, 0.0, 0.0, gx, 0.0, profile_col);
+    CUDA_OR(cudaGetLastError());
+    obs_final_kernel<<<1, 32, 0, s>>>(scratch, L);
+    CUDA_OR(cudaGetLastError());
+    // straight into the caller's arrays or small stack buffers: no allocation here
+    double part[4];
+    double prof[kNoAllocMaxNy];
+    CUDA_OR(cudaMemcpyAsync(part, scratch + L.part, sizeof part, cudaMemcpyDeviceToHost, s));
+    CUDA_OR(cudaMemcpyAsync(prof, scratch + L.prof_x, ny * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (uy_prof) CUDA_OR(cudaMemcpyAsync(uy_prof, scratch + L.prof_y, ny * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (m_of_x) CUDA_OR(cudaMemcpyAsync(m_of_x, scratch + L.m, nx * sizeof(double), cudaMemcpyDeviceToHost, s));
+    double* rc_dst = p_centre ? p_centre : dp_nonlin;
+    if (rc_dst) CUDA_OR(cudaMemcpyAsync(rc_dst, scratch + L.rc, nx * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_OR(cudaStreamSynchronize(s));
+
+    const double p_in = rho_in / 3.0, p_out = rho_out / 3.0;
+    const double Lx = nx > 1 ? (double)(nx - 1) : 1.0;
+    if (rc_dst)
+        for (int x = 0; x < nx; ++x) {
+            const double pc = rc_dst[x] / 3.0;  // centreline density -> pressure
+            if (p_centre) p_centre[x] = pc;
+            if (dp_nonlin) dp_nonlin[x] = (pc - (p_in - (p_in - p_out) * x / Lx)) / p_out;
+        }
+    double umax = -INFINITY;
+    for (int y = 0; y < ny; ++y) {
+        if (ux_prof) ux_prof[y] = prof[y];
+        umax = std::max(umax, prof[y]);
+    }
+    if (sc) {
+        const double mbar = part[0] / nx;
+        sc->mass_flow = mbar;
+        sc->u_slip = ny >= 2 ? 0.5 * ((1.5 * prof[0] - 0.5 * prof[1]) + (1.5 * prof[ny - 1] - 0.5 * prof[ny - 2]))
+                             : prof[0];
+        if (drive == CLB_DRIVE_BODY_FORCE) {
+            sc->q_norm = g != 0 ? (part[1] / nx) / (3.0 * g * (double)ny * ny * std::sqrt(1.0 / 6.0)) : 0.0;
+        } else {
+            const double mu = rho_out * std::sqrt(6.0 / kPi) * kn * ny / 3.0;
+            const double mns = (double)ny * ny * ny * (p_in * p_in - p_out * p_out) / (24.0 * mu * (1.0 / 3.0) * Lx);
+            sc->q_norm = mbar / mns;
+        }
+        sc->residual = -1.0;  // no previous call to compare with: the entry point keeps no state
+        sc->total_mass = part[2];
+        sc->ux_max = umax;
+        sc->step = -1;
+    }
+    if (part[3] > 0)
+        return fail(CLB_ENUMERIC, "clb_observables_noalloc: %.0f nodes with a non-finite density or velocity",
+                    part[3]);
+    return CLB_OK;
+}
