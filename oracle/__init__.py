@@ -12,6 +12,8 @@ from .oracle import (  # noqa: F401
     build_oracle,
     collide,
     feq,
+    flow_sum_cs,
+    gradient_cs,
     kmat,
     lattice,
     load,

@@ -51,6 +51,22 @@
 
 #define NQ 9
 
+/* In the complex-step build (ORACLE_COMPLEX) every quantity that depends on
+ * the state or on r, a or F carries an imaginary part: perturbing one of them
+ * by i*h gives its exact derivative as Im(result)/h, with no cancellation.
+ * The ordinary build has real_t = double and is unchanged arithmetic. */
+#ifdef ORACLE_COMPLEX
+#define RE(v) creal(v)
+static real_t P_r(const oracle_params* p) { return p->r + I * p->r_im; }
+static real_t P_a(const oracle_params* p) { return p->a + I * p->a_im; }
+static real_t P_gx(const oracle_params* p) { return p->gx + I * p->gx_im; }
+#else
+#define RE(v) (v)
+static real_t P_r(const oracle_params* p) { return p->r; }
+static real_t P_a(const oracle_params* p) { return p->a; }
+static real_t P_gx(const oracle_params* p) { return p->gx; }
+#endif
+
 static const double PI = 3.14159265358979323846;
 
 /* ------------------------------------------------------------------ lattice */
@@ -170,27 +186,27 @@ static void ensure_tables(void)
 }
 
 /* Raw moment <ex^m ey^n | f> (the inner product defined under Eq. 7). */
-static double raw_moment(const double f[9], int m, int n)
+static real_t raw_moment(const real_t f[9], int m, int n)
 {
-    double s = 0.0;
+    real_t s = 0.0;
     for (int i = 0; i < NQ; ++i) s += (double)(ipow(EX[i], m) * ipow(EY[i], n)) * f[i];
     return s;
 }
 
-static void tinv_apply(const double m[9], double f[9])
+static void tinv_apply(const real_t m[9], real_t f[9])
 {
     for (int i = 0; i < NQ; ++i) {
-        double s = 0.0;
+        real_t s = 0.0;
         for (int j = 0; j < NQ; ++j) s += TINV[i * 9 + j] * m[j];
         f[i] = s;
     }
 }
 
 /* Eq. 11 */
-void oracle_feq(double rho, double ux, double uy, double out[9])
+void oracle_feq(real_t rho, real_t ux, real_t uy, real_t out[9])
 {
     ensure_tables();
-    double m[9];
+    real_t m[9];
     m[0] = rho;
     m[1] = rho * ux;
     m[2] = rho * uy;
@@ -208,11 +224,11 @@ void oracle_feq(double rho, double ux, double uy, double out[9])
 /* Eq. 18: 1/s_v = 1/2 + sqrt(6/pi) N Kn / (1 + a Kn), N = H/dx = ny (walls half
  * a cell outside the first and last rows).
  * Eq. 21: 1/s_q = 1/2 + (3 + 4 pi tau_q^2 B2) / (16 tau_q), tau_q = 1/s_v - 1/2. */
-void oracle_rates_kn(double kn_local, int ny, double a, double b2, double* sv, double* sq)
+void oracle_rates_kn(real_t kn_local, int ny, real_t a, real_t b2, real_t* sv, real_t* sq)
 {
-    const double inv_sv = 0.5 + sqrt(6.0 / PI) * (double)ny * kn_local / (1.0 + a * kn_local);
-    const double tq = inv_sv - 0.5;
-    const double inv_sq = 0.5 + (3.0 + 4.0 * PI * tq * tq * b2) / (16.0 * tq);
+    const real_t inv_sv = 0.5 + sqrt(6.0 / PI) * (double)ny * kn_local / (1.0 + a * kn_local);
+    const real_t tq = inv_sv - 0.5;
+    const real_t inv_sq = 0.5 + (3.0 + 4.0 * PI * tq * tq * b2) / (16.0 * tq);
     *sv = 1.0 / inv_sv;
     *sq = 1.0 / inv_sq;
 }
@@ -227,26 +243,26 @@ double oracle_r_from_sigma(double sigma)
 
 /* --------------------------------------------------------------- collision */
 
-void oracle_collide(const double fb[9], double Fx, double Fy, const double s[9],
-                    double out[9], double ghat[9], double Sout[9])
+void oracle_collide(const real_t fb[9], real_t Fx, real_t Fy, const real_t s[9],
+                    real_t out[9], real_t ghat[9], real_t Sout[9])
 {
     ensure_tables();
     /* Eq. 12 and the raw moments of Eq. 8 */
-    const double rho = raw_moment(fb, 0, 0);
-    const double kx = raw_moment(fb, 1, 0);
-    const double ky = raw_moment(fb, 0, 1);
-    const double kxx = raw_moment(fb, 2, 0);
-    const double kyy = raw_moment(fb, 0, 2);
-    const double kxy = raw_moment(fb, 1, 1);
-    const double kxxy = raw_moment(fb, 2, 1);
-    const double kxyy = raw_moment(fb, 1, 2);
-    const double kxxyy = raw_moment(fb, 2, 2);
+    const real_t rho = raw_moment(fb, 0, 0);
+    const real_t kx = raw_moment(fb, 1, 0);
+    const real_t ky = raw_moment(fb, 0, 1);
+    const real_t kxx = raw_moment(fb, 2, 0);
+    const real_t kyy = raw_moment(fb, 0, 2);
+    const real_t kxy = raw_moment(fb, 1, 1);
+    const real_t kxxy = raw_moment(fb, 2, 1);
+    const real_t kxyy = raw_moment(fb, 1, 2);
+    const real_t kxxyy = raw_moment(fb, 2, 2);
     /* Eq. 13 (delta_t = 1) */
-    const double ux = (kx + 0.5 * rho * Fx) / rho;
-    const double uy = (ky + 0.5 * rho * Fy) / rho;
+    const real_t ux = (kx + 0.5 * rho * Fx) / rho;
+    const real_t uy = (ky + 0.5 * rho * Fy) / rho;
 
     /* Eq. 7, in order: each kernel uses the lower ones */
-    double g[9];
+    real_t g[9];
     g[0] = g[1] = g[2] = 0.0;
     g[3] = s[3] / 12.0 *
            (2.0 / 3.0 * rho + rho * (ux * ux + uy * uy) - (kxx + kyy) -
@@ -271,7 +287,7 @@ void oracle_collide(const double fb[9], double Fx, double Fy, const double s[9],
            4.0 * ux * uy * g[5] - 2.0 * uy * g[6] - 2.0 * ux * g[7];
 
     /* Eq. 9 and S = T^-1 S^ (Eq. 10) */
-    double Sh[9], S[9];
+    real_t Sh[9], S[9];
     Sh[0] = 0.0;
     Sh[1] = rho * Fx;
     Sh[2] = rho * Fy;
@@ -285,7 +301,7 @@ void oracle_collide(const double fb[9], double Fx, double Fy, const double s[9],
 
     /* Eq. 4: f~ = fbar + K g^ + S  (delta_t = 1) */
     for (int i = 0; i < NQ; ++i) {
-        double kg = 0.0;
+        real_t kg = 0.0;
         for (int j = 0; j < NQ; ++j) kg += KMAT[i * 9 + j] * g[j];
         out[i] = fb[i] + kg + S[i];
     }
@@ -299,9 +315,9 @@ void oracle_collide(const double fb[9], double Fx, double Fy, const double s[9],
 
 struct oracle_sim {
     oracle_params p;
-    double* ft; /* post-collision state, [9][ny][nx] */
-    double* fb; /* work: pre-collision populations */
-    double sv_const, sq_const;
+    real_t* ft; /* post-collision state, [9][ny][nx] */
+    real_t* fb; /* work: pre-collision populations */
+    real_t sv_const, sq_const;
 };
 
 static int g_threads_used = 1;
@@ -310,11 +326,11 @@ int oracle_threads_used(void) { return g_threads_used; }
 
 #define IDX(i, y, x, nx, ny) ((((size_t)(i)) * (size_t)(ny) + (size_t)(y)) * (size_t)(nx) + (size_t)(x))
 
-static void node_rates(const oracle_params* p, double rho, double s[9])
+static void node_rates(const oracle_params* p, real_t rho, real_t s[9])
 {
-    double sv, sq;
-    const double kn_local = p->pressure ? p->kn * p->rho_out / rho : p->kn;
-    oracle_rates_kn(kn_local, p->ny, p->a, p->b2, &sv, &sq);
+    real_t sv, sq;
+    const real_t kn_local = p->pressure ? p->kn * p->rho_out / rho : p->kn;
+    oracle_rates_kn(kn_local, p->ny, P_a(p), p->b2, &sv, &sq);
     if (p->sv_override > 0.0) sv = p->sv_override;
     if (p->sq_override > 0.0) sq = p->sq_override;
     s[0] = s[1] = s[2] = 0.0;
@@ -332,13 +348,13 @@ oracle_sim* oracle_create(const oracle_params* p)
     oracle_sim* s = (oracle_sim*)calloc(1, sizeof(oracle_sim));
     s->p = *p;
     const size_t n = (size_t)NQ * p->nx * p->ny;
-    s->ft = (double*)malloc(n * sizeof(double));
-    s->fb = (double*)malloc(n * sizeof(double));
+    s->ft = (real_t*)malloc(n * sizeof(real_t));
+    s->fb = (real_t*)malloc(n * sizeof(real_t));
     for (int x = 0; x < p->nx; ++x) {
-        double rho0 = p->rho_out;
+        real_t rho0 = p->rho_out;
         if (p->pressure)
             rho0 = p->rho_in + (p->rho_out - p->rho_in) * (double)x / (double)(p->nx - 1);
-        double feq[9];
+        real_t feq[9];
         oracle_feq(rho0, 0.0, 0.0, feq);
         for (int y = 0; y < p->ny; ++y)
             for (int i = 0; i < NQ; ++i) s->ft[IDX(i, y, x, p->nx, p->ny)] = feq[i];
@@ -354,14 +370,14 @@ void oracle_destroy(oracle_sim* s)
     free(s);
 }
 
-void oracle_get_state(const oracle_sim* s, double* f)
+void oracle_get_state(const oracle_sim* s, real_t* f)
 {
-    memcpy(f, s->ft, (size_t)NQ * s->p.nx * s->p.ny * sizeof(double));
+    memcpy(f, s->ft, (size_t)NQ * s->p.nx * s->p.ny * sizeof(real_t));
 }
 
-void oracle_set_state(oracle_sim* s, const double* f)
+void oracle_set_state(oracle_sim* s, const real_t* f)
 {
-    memcpy(s->ft, f, (size_t)NQ * s->p.nx * s->p.ny * sizeof(double));
+    memcpy(s->ft, f, (size_t)NQ * s->p.nx * s->p.ny * sizeof(real_t));
 }
 
 /* Wrap an x index in periodic mode; -1 if it leaves a pressure channel. */
@@ -374,10 +390,10 @@ static int xsrc(const oracle_params* p, int x)
 
 /* Eq. 20 and its mirror: the populations entering row 0 from the bottom wall
  * and row ny-1 from the top wall, at column x, from the post-collision state. */
-static double wall_value(const oracle_params* p, const double* ft, int i, int y, int x)
+static real_t wall_value(const oracle_params* p, const real_t* ft, int i, int y, int x)
 {
     const int nx = p->nx, ny = p->ny;
-    const double r = p->r;
+    const real_t r = P_r(p);
     const int xm = p->same_node_bsr ? x : xsrc(p, x - 1);
     const int xp = p->same_node_bsr ? x : xsrc(p, x + 1);
     if (y == 0 && (i == 2 || i == 5 || i == 6)) {
@@ -400,7 +416,7 @@ static double wall_value(const oracle_params* p, const double* ft, int i, int y,
     return r * ft[IDX(6, yt, x, nx, ny)] + (1.0 - r) * ft[IDX(5, yt, xm, nx, ny)];
 }
 
-static void macro_of(const double f[9], double Fx, double Fy, double* rho, double* ux, double* uy)
+static void macro_of(const real_t f[9], real_t Fx, real_t Fy, real_t* rho, real_t* ux, real_t* uy)
 {
     /* Eq. 12-13 on pre-collision populations */
     *rho = raw_moment(f, 0, 0);
@@ -411,19 +427,19 @@ static void macro_of(const double f[9], double Fx, double Fy, double* rho, doubl
 /* Pressure column rebuild (reading of Sec. 3.2, see file header).
  * f1, f2: pre-collision populations of the first and second interior
  * neighbours; rho_b: imposed density; out: the boundary populations. */
-static void pressure_rebuild(const oracle_params* p, const double f1[9], const double f2[9],
-                             double rho_b, double out[9])
+static void pressure_rebuild(const oracle_params* p, const real_t f1[9], const real_t f2[9],
+                             real_t rho_b, real_t out[9])
 {
-    double r1, u1x, u1y, r2, u2x, u2y, e1[9], eb[9];
-    macro_of(f1, p->gx, p->gy, &r1, &u1x, &u1y);
-    macro_of(f2, p->gx, p->gy, &r2, &u2x, &u2y);
+    real_t r1, u1x, u1y, r2, u2x, u2y, e1[9], eb[9];
+    macro_of(f1, P_gx(p), p->gy, &r1, &u1x, &u1y);
+    macro_of(f2, P_gx(p), p->gy, &r2, &u2x, &u2y);
     oracle_feq(r1, u1x, u1y, e1);
     oracle_feq(rho_b, 2.0 * u1x - u2x, 2.0 * u1y - u2y, eb);
     for (int i = 0; i < NQ; ++i) out[i] = eb[i] + (f1[i] - e1[i]);
 }
 
 /* Steps 1-3 of a time step: streaming, walls, pressure columns. */
-static void stream_and_boundaries(const oracle_params* p, const double* ft, double* fb, int nthreads)
+static void stream_and_boundaries(const oracle_params* p, const real_t* ft, real_t* fb, int nthreads)
 {
     const int nx = p->nx, ny = p->ny;
     const size_t n = (size_t)NQ * nx * ny;
@@ -454,7 +470,7 @@ static void stream_and_boundaries(const oracle_params* p, const double* ft, doub
     /* 3. pressure columns, from the streamed interior columns */
     if (p->pressure) {
         for (int y = 0; y < ny; ++y) {
-            double a1[9], a2[9], b1[9], b2[9], in[9], outc[9];
+            real_t a1[9], a2[9], b1[9], b2[9], in[9], outc[9];
             for (int i = 0; i < NQ; ++i) {
                 a1[i] = fb[IDX(i, y, 1, nx, ny)];
                 a2[i] = fb[IDX(i, y, 2, nx, ny)];
@@ -471,7 +487,7 @@ static void stream_and_boundaries(const oracle_params* p, const double* ft, doub
     }
 }
 
-static void collide_all(const oracle_params* p, const double* fb, double* ft, int nthreads)
+static void collide_all(const oracle_params* p, const real_t* fb, real_t* ft, int nthreads)
 {
     const int nx = p->nx, ny = p->ny;
 #pragma omp parallel for num_threads(nthreads) schedule(static)
@@ -480,10 +496,10 @@ static void collide_all(const oracle_params* p, const double* fb, double* ft, in
         if (y == 0) g_threads_used = omp_get_num_threads();
 #endif
         for (int x = 0; x < nx; ++x) {
-            double f[9], o[9], s[9];
+            real_t f[9], o[9], s[9];
             for (int i = 0; i < NQ; ++i) f[i] = fb[IDX(i, y, x, nx, ny)];
             node_rates(p, raw_moment(f, 0, 0), s);
-            oracle_collide(f, p->gx, p->gy, s, o, NULL, NULL);
+            oracle_collide(f, P_gx(p), p->gy, s, o, NULL, NULL);
             for (int i = 0; i < NQ; ++i) ft[IDX(i, y, x, nx, ny)] = o[i];
         }
     }
@@ -510,7 +526,7 @@ int64_t oracle_step(oracle_sim* s, int64_t nsteps, int nthreads)
     return nsteps;
 }
 
-void oracle_prestate(oracle_sim* s, double* fbar)
+void oracle_prestate(oracle_sim* s, real_t* fbar)
 {
     stream_and_boundaries(&s->p, s->ft, fbar, 1);
 }
@@ -519,11 +535,11 @@ void oracle_prestate(oracle_sim* s, double* fbar)
 
 /* Pre-collision populations at (x, y): what streaming, the walls and the
  * pressure columns deliver there, gathered node by node. */
-static void arrive(const oracle_params* p, const double* ft, int x, int y, double fb[9])
+static void arrive(const oracle_params* p, const real_t* ft, int x, int y, real_t fb[9])
 {
     const int nx = p->nx, ny = p->ny;
     if (p->pressure && (x == 0 || x == nx - 1)) {
-        double f1[9], f2[9];
+        real_t f1[9], f2[9];
         const int d = (x == 0) ? 1 : -1;
         arrive(p, ft, x + d, y, f1);
         arrive(p, ft, x + 2 * d, y, f2);
@@ -541,15 +557,15 @@ static void arrive(const oracle_params* p, const double* ft, int x, int y, doubl
     }
 }
 
-void oracle_step_nodes(const oracle_params* p, const double* f_prev, int n, const int* xs,
-                       const int* ys, double* out)
+void oracle_step_nodes(const oracle_params* p, const real_t* f_prev, int n, const int* xs,
+                       const int* ys, real_t* out)
 {
     ensure_tables();
     for (int k = 0; k < n; ++k) {
-        double fb[9], s[9];
+        real_t fb[9], s[9];
         arrive(p, f_prev, xs[k], ys[k], fb);
         node_rates(p, raw_moment(fb, 0, 0), s);
-        oracle_collide(fb, p->gx, p->gy, s, out + 9 * (size_t)k, NULL, NULL);
+        oracle_collide(fb, P_gx(p), p->gy, s, out + 9 * (size_t)k, NULL, NULL);
     }
 }
 
@@ -558,22 +574,22 @@ void oracle_step_nodes(const oracle_params* p, const double* f_prev, int n, cons
 /* Density and velocity at a node from its post-collision populations: the
  * collision keeps rho and adds rho F to the first moment (Eq. 4, 9), so
  * rho u = sum e_i f~_i - rho F / 2 equals Eq. 13 at the same time level. */
-static void node_macro(const oracle_sim* s, int x, int y, double* rho, double* ux, double* uy)
+static void node_macro(const oracle_sim* s, int x, int y, real_t* rho, real_t* ux, real_t* uy)
 {
     const oracle_params* p = &s->p;
-    double f[9];
+    real_t f[9];
     for (int i = 0; i < NQ; ++i) f[i] = s->ft[IDX(i, y, x, p->nx, p->ny)];
     *rho = raw_moment(f, 0, 0);
-    *ux = (raw_moment(f, 1, 0) - 0.5 * (*rho) * p->gx) / (*rho);
+    *ux = (raw_moment(f, 1, 0) - 0.5 * (*rho) * P_gx(p)) / (*rho);
     *uy = (raw_moment(f, 0, 1) - 0.5 * (*rho) * p->gy) / (*rho);
 }
 
-void oracle_macro(const oracle_sim* s, double* rho, double* ux, double* uy)
+void oracle_macro(const oracle_sim* s, real_t* rho, real_t* ux, real_t* uy)
 {
     const int nx = s->p.nx, ny = s->p.ny;
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
-            double r, a, b;
+            real_t r, a, b;
             node_macro(s, x, y, &r, &a, &b);
             if (rho) rho[(size_t)y * nx + x] = r;
             if (ux) ux[(size_t)y * nx + x] = a;
@@ -581,21 +597,21 @@ void oracle_macro(const oracle_sim* s, double* rho, double* ux, double* uy)
         }
 }
 
-void oracle_observables(const oracle_sim* s, int profile_col, double scal[5], double* ux_prof,
-                        double* uy_prof, double* p_centre, double* dp_nonlin, double* m_of_x)
+void oracle_observables(const oracle_sim* s, int profile_col, real_t scal[5], real_t* ux_prof,
+                        real_t* uy_prof, real_t* p_centre, real_t* dp_nonlin, real_t* m_of_x)
 {
     const oracle_params* p = &s->p;
     const int nx = p->nx, ny = p->ny;
     if (profile_col < 0 || profile_col >= nx) profile_col = p->pressure ? nx - 1 : 0;
-    const double p_in = (p->pressure ? p->rho_in : p->rho_out) / 3.0;
-    const double p_out = p->rho_out / 3.0;
-    const double L = (nx > 1) ? (double)(nx - 1) : 1.0;
+    const real_t p_in = (p->pressure ? p->rho_in : p->rho_out) / 3.0;
+    const real_t p_out = p->rho_out / 3.0;
+    const real_t L = (nx > 1) ? (double)(nx - 1) : 1.0;
 
-    double msum = 0.0, mass = 0.0, usum = 0.0;
+    real_t msum = 0.0, mass = 0.0, usum = 0.0;
     for (int x = 0; x < nx; ++x) {
-        double mx = 0.0, ucol = 0.0, rc = 0.0;
+        real_t mx = 0.0, ucol = 0.0, rc = 0.0;
         for (int y = 0; y < ny; ++y) {
-            double rho, ux, uy;
+            real_t rho, ux, uy;
             node_macro(s, x, y, &rho, &ux, &uy);
             mx += rho * ux;
             ucol += ux;
@@ -606,46 +622,46 @@ void oracle_observables(const oracle_sim* s, int profile_col, double scal[5], do
         }
         msum += mx;
         usum += ucol;
-        const double pc = rc / 3.0;
+        const real_t pc = rc / 3.0;
         /* Sec. 3.2: p_l decreases linearly from p_in to p_out over L */
-        const double pl = p_in - (p_in - p_out) * (double)x / L;
+        const real_t pl = p_in - (p_in - p_out) * (double)x / L;
         if (m_of_x) m_of_x[x] = mx;
         if (p_centre) p_centre[x] = pc;
         if (dp_nonlin) dp_nonlin[x] = (pc - pl) / p_out;
     }
-    double umax = -INFINITY;
-    double ucol_prof[4] = {0, 0, 0, 0};
+    real_t umax = -INFINITY;
+    real_t ucol_prof[4] = {0, 0, 0, 0};
     for (int y = 0; y < ny; ++y) {
-        double rho, ux, uy;
+        real_t rho, ux, uy;
         node_macro(s, profile_col, y, &rho, &ux, &uy);
         if (ux_prof) ux_prof[y] = ux;
         if (uy_prof) uy_prof[y] = uy;
-        if (ux > umax) umax = ux;
+        if (RE(ux) > RE(umax)) umax = ux;
         if (y < 2) ucol_prof[y] = ux;
         if (y >= ny - 2) ucol_prof[2 + (y - (ny - 2))] = ux;
     }
-    double slip;
+    real_t slip;
     if (ny >= 2) {
         /* linear extrapolation of the first two rows to the wall at half a cell */
-        const double sb = 1.5 * ucol_prof[0] - 0.5 * ucol_prof[1];
-        const double st = 1.5 * ucol_prof[3] - 0.5 * ucol_prof[2];
+        const real_t sb = 1.5 * ucol_prof[0] - 0.5 * ucol_prof[1];
+        const real_t st = 1.5 * ucol_prof[3] - 0.5 * ucol_prof[2];
         slip = 0.5 * (sb + st);
     } else {
         slip = ucol_prof[0];
     }
-    const double mbar = msum / (double)nx;
-    double qnorm = 0.0;
+    const real_t mbar = msum / (double)nx;
+    real_t qnorm = 0.0;
     if (!p->pressure) {
         /* Sec. 3.1: Q = int u dy / (F H^2 sqrt(RT/2) / p), RT = 1/3, p = rho0 RT,
          * F = rho0 g, so Q = sum_y u / (3 g H^2 sqrt(1/6)). */
         if (p->gx != 0.0)
-            qnorm = (usum / (double)nx) / (3.0 * p->gx * (double)ny * (double)ny * sqrt(1.0 / 6.0));
+            qnorm = (usum / (double)nx) / (3.0 * P_gx(p) * (double)ny * (double)ny * sqrt(1.0 / 6.0));
     } else {
         /* Sec. 3.2: S = m / m_ns; m_ns is the isothermal no-slip flow with the
          * unreduced viscosity mu = rho_out sqrt(6/pi) Kn_out N / 3 (Eq. 17 with a = 0):
          * m_ns = H^3 (p_in^2 - p_out^2) / (24 mu RT L). */
-        const double mu = p->rho_out * sqrt(6.0 / PI) * p->kn * (double)ny / 3.0;
-        const double mns = (double)ny * ny * ny * (p_in * p_in - p_out * p_out) / (24.0 * mu * (1.0 / 3.0) * L);
+        const real_t mu = p->rho_out * sqrt(6.0 / PI) * p->kn * (double)ny / 3.0;
+        const real_t mns = (double)ny * ny * ny * (p_in * p_in - p_out * p_out) / (24.0 * mu * (1.0 / 3.0) * L);
         qnorm = mbar / mns;
     }
     if (scal) {

@@ -17,25 +17,30 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "clb_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle_clb.so")
+_LIB_CS = os.path.join(_HERE, "liboracle_clb_cs.so")  # complex-step build
 
 _lib = None
+_lib_cs = None
+
+
+def _fresh(lib):
+    return os.path.exists(lib) and os.path.getmtime(lib) >= max(os.path.getmtime(_SRC),
+                                                               os.path.getmtime(_SRC[:-1] + "h"))
 
 
 def build_oracle(force: bool = False) -> str:
-    """Compile the oracle shared library in place; returns its path."""
-    if (
-        not force
-        and os.path.exists(_LIB)
-        and os.path.getmtime(_LIB) >= max(os.path.getmtime(_SRC), os.path.getmtime(_SRC[:-1] + "h"))
-    ):
-        return _LIB
-    tmp = _LIB + ".tmp%d" % os.getpid()
-    cmd = [
-        "gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
-        "-o", tmp, _SRC, "-lm",
-    ]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB)
+    """Compile the oracle shared libraries in place (the FP64 oracle and its
+    complex-step build); returns the FP64 one's path."""
+    for lib, extra in ((_LIB, []), (_LIB_CS, ["-DORACLE_COMPLEX"])):
+        if not force and _fresh(lib):
+            continue
+        tmp = lib + ".tmp%d" % os.getpid()
+        cmd = [
+            "gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", *extra,
+            "-o", tmp, _SRC, "-lm",
+        ]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, lib)
     return _LIB
 
 
@@ -47,6 +52,7 @@ class _Params(C.Structure):
         ("rho_in", C.c_double), ("rho_out", C.c_double),
         ("sv_override", C.c_double), ("sq_override", C.c_double),
         ("same_node_bsr", C.c_int),
+        ("r_im", C.c_double), ("a_im", C.c_double), ("gx_im", C.c_double),
     ]
 
 
@@ -71,13 +77,16 @@ class OracleParams:
     sv_override: float = 0.0
     sq_override: float = 0.0
     same_node_bsr: bool = False
+    r_im: float = 0.0  # imaginary parts, read by the complex-step build only
+    a_im: float = 0.0
+    gx_im: float = 0.0
 
     def c(self) -> _Params:
         r = self.r if self.r is not None else r_from_sigma(self.sigma)
         return _Params(
             self.nx, self.ny, int(self.pressure), self.kn, self.a, r, self.b2, self.s3, self.s8,
             self.gx, self.gy, self.rho_in, self.rho_out, self.sv_override, self.sq_override,
-            int(self.same_node_bsr),
+            int(self.same_node_bsr), self.r_im, self.a_im, self.gx_im,
         )
 
 
@@ -256,3 +265,59 @@ class OracleSim:
             ux_prof=uxp, uy_prof=uyp, p_centre=pc, dp_nonlin=dp, m_of_x=mx,
         )
 
+
+
+# ------------------------------------------------------ complex-step gradient
+
+def load_cs():
+    """The complex-step build: every real_t is a (re, im) pair of doubles."""
+    global _lib_cs
+    if _lib_cs is not None:
+        return _lib_cs
+    build_oracle()
+    lib = C.CDLL(_LIB_CS)
+    P = C.c_void_p
+    lib.oracle_create.argtypes = [C.POINTER(_Params)]
+    lib.oracle_create.restype = P
+    lib.oracle_destroy.argtypes = [P]
+    lib.oracle_step.argtypes = [P, C.c_int64, C.c_int]
+    lib.oracle_step.restype = C.c_int64
+    lib.oracle_macro.argtypes = [P, P, P, P]
+    lib.oracle_get_state.argtypes = [P, P]
+    _lib_cs = lib
+    return lib
+
+
+def flow_sum_cs(params: OracleParams, nsteps: int, threads: int = 1):
+    """J = mean over x of sum_y u_x after nsteps (complex-step build): returns
+    the complex J and the complex state; Im parts carry the perturbation."""
+    lib = load_cs()
+    p = params.c()
+    h = lib.oracle_create(C.byref(p))
+    if not h:
+        raise ValueError("oracle_create rejected the parameters")
+    try:
+        lib.oracle_step(h, int(nsteps), int(threads))
+        ny, nx = params.ny, params.nx
+        ux = np.zeros((ny, nx), np.complex128)
+        lib.oracle_macro(h, None, ux.ctypes.data, None)
+        return ux.sum() / nx
+    finally:
+        lib.oracle_destroy(h)
+
+
+def gradient_cs(params: OracleParams, nsteps: int, h: float = 1e-30, threads: int = 1):
+    """Exact derivatives of J = mean_x sum_y u_x after nsteps with respect to
+    r, a and G (gx), by complex-step differentiation: J(theta + i h) has
+    imaginary part h dJ/dtheta + O(h^3).  Returns (J, {"r", "a", "g"})."""
+    from dataclasses import replace
+
+    if params.r is None:
+        params = replace(params, r=r_from_sigma(params.sigma))
+    out = {}
+    J = None
+    for name, field in (("r", "r_im"), ("a", "a_im"), ("g", "gx_im")):
+        Jc = flow_sum_cs(replace(params, **{field: h}), nsteps, threads)
+        out[name] = Jc.imag / h
+        J = Jc.real
+    return J, out
