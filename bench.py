@@ -3,7 +3,8 @@
 Workload: the L/H = 100 pressure-driven microchannel of Sec. 3.2 at
 Ny = 256, Nx = 25601 (6,553,856 nodes), Kn_out = 0.1, p_in/p_out = 2.47,
 populations stored as FP32 deviations (the headline) and, for comparison, in
-FP64.  One step = one fused sweep over every node; the timed region also holds
+FP64, FP16 (x 2^14) and BF16, each with the error of its mass flow and
+pressure deviation against the FP64 oracle after the CPU-baseline steps.  One step = one fused sweep over every node; the timed region also holds
 one FP64 observable reduction (mass flow, centreline pressure, profiles).
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
@@ -241,7 +242,6 @@ def run_gpu(args):
     if rank != 0:
         return None
     f32 = results["fp32s"]
-    f64 = results.get("fp64")
     peak, peak_kind = measured_peaks()
     achieved = f32["bytes_per_node"] * nodes / (f32["sweep_us"] * 1e-6) / 1e9
     traffic = profiled_traffic("fp32s")
@@ -278,7 +278,7 @@ def run_gpu(args):
             "bytes_per_node": f32["bytes_per_node"],
             "kernel": "sweep_kernel<float, pressure, 4>",
         },
-        "variants": variants_block(f32, f64, nodes, peak),
+        "variants": variants_block(results, nodes, peak),
         "e2e": {
             "value": round(world * nodes * K / t_e2e / 1e6, 1),
             "unit": "MLUPS",
@@ -290,19 +290,103 @@ def run_gpu(args):
         "gpu_launches": K + 2,
         "clocks": clocks,
     }
-    line["cpu_baseline"] = cpu_baseline(args.cpu_seconds) if not args.no_cpu_baseline else None
+    if not args.no_batch:
+        line["knudsen_sweep"] = knudsen_sweep_bench(clb, torch, args.batch_steps)
+    if args.no_cpu_baseline or world > 1:
+        line["cpu_baseline"] = None
+    else:
+        base, ref = cpu_baseline(args.cpu_steps)
+        line["cpu_baseline"] = base
+        line["errors_vs_oracle"] = errors_vs_oracle(clb, args.variants, ref, args.cpu_steps)
     return line
 
 
-def variants_block(f32, f64, nodes, peak):
-    out = {"fp32s": {"mlups": round(f32["mlups"], 1), "sweep_us": round(f32["sweep_us"], 3),
-                     "mass_flow": f32["mass_flow"]}}
-    if f64 is not None:
-        out["fp64"] = {"mlups": round(f64["mlups"], 1), "sweep_us": round(f64["sweep_us"], 3),
-                       "mass_flow": f64["mass_flow"],
-                       "hbm_frac": round(f64["bytes_per_node"] * nodes / (f64["sweep_us"] * 1e-6) / 1e9 / peak, 4),
-                       "clocks": f64["clocks"]}
-        out["fp32s_over_fp64"] = round(f32["mlups"] / f64["mlups"], 3)
+def knudsen_sweep_bench(clb, torch, steps):
+    """The batched Knudsen sweep of Sec. 3.1 (48 periodic channels, Kn
+    log-spaced over 0.01..10, ny cycling 16/32/64/128, nx = 4, G = 1e-6,
+    FP32-shifted): aggregate MLUPS of the persistent, graph-replayed launch
+    against one ordinary sweep launch per channel per step."""
+    n = 48
+    kn = [10 ** (-2 + 3 * k / (n - 1)) for k in range(n)]
+    ny = [(16, 32, 64, 128)[k % 4] for k in range(n)]
+    nx = [4] * n
+    nodes = sum(a * b for a, b in zip(nx, ny))
+    b = clb.Batch(nx, ny, kn, g=1e-6, storage="fp32s")
+    b.step(1000)  # autotunes, then warms up
+    b.stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(b.stream)
+    b.step(steps)
+    e1.record(b.stream)
+    e1.synchronize()
+    t_batch = e0.elapsed_time(e1) / 1e3
+    q = [o["q_norm"] for o in b.observables()]
+    block = b.info()["block_x"]
+    b.close()
+    stream = torch.cuda.Stream()
+    chans = [clb.Channel(nx[k], ny[k], kn[k], drive="body_force", drive_value=1e-6, storage="fp32s",
+                         stream=stream) for k in range(n)]
+    rounds = max(50, steps // 40)
+    for c in chans:
+        c.step(20)
+    stream.synchronize()
+    e0.record(stream)
+    for _ in range(rounds):
+        for c in chans:
+            c.step(1)
+    e1.record(stream)
+    e1.synchronize()
+    t_sep = e0.elapsed_time(e1) / 1e3
+    for c in chans:
+        c.close()
+    i = min(range(n), key=lambda k: q[k])
+    return {
+        "workload": "48 periodic channels, Kn = 10^(-2+3k/47), ny cycling 16/32/64/128, nx = 4, G = 1e-6, fp32s",
+        "nodes": nodes,
+        "mlups_persistent": round(nodes * steps / t_batch / 1e6, 1),
+        "us_per_step_persistent": round(t_batch / steps * 1e6, 3),
+        "mlups_separate_launches": round(nodes * rounds / t_sep / 1e6, 1),
+        "us_per_step_separate_launches": round(t_sep / rounds * 1e6, 3),
+        "speedup": round((nodes * steps / t_batch) / (nodes * rounds / t_sep), 2),
+        "block_x_tuned": block,
+        "steps": steps,
+        "q_min_kn_after_steps": kn[i],
+    }
+
+
+def errors_vs_oracle(clb, variants, ref, steps):
+    """Each storage variant after `steps` steps from the initial state, against
+    the FP64 oracle run of the CPU-baseline leg (same steps, same channel)."""
+    import numpy as np
+
+    out = {"steps": steps}
+    x = np.arange(NX)
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)[:, None, None]
+    dev = np.abs(ref["state"] - w * (RATIO + (1.0 - RATIO) * x / (NX - 1))[None, None, :]).max()
+    for storage in variants:
+        ch = clb.Channel(NX, NY, KN_OUT, drive="pressure", drive_value=RATIO, storage=storage)
+        ch.step(steps)
+        o = ch.observables()
+        f = ch.state()
+        ch.close()
+        out[storage] = {
+            "mass_flow_rel": abs(o["mass_flow"] - ref["mass_flow"]) / abs(ref["mass_flow"]),
+            "dp_nonlin_abs_max": float(np.abs(o["dp_nonlin"] - ref["dp_nonlin"]).max()),
+            "population_abs_max_over_max_deviation": float(np.abs(f - ref["state"]).max() / dev),
+        }
+        del f
+    return out
+
+
+def variants_block(results, nodes, peak):
+    out = {}
+    for storage, r in results.items():
+        out[storage] = {"mlups": round(r["mlups"], 1), "sweep_us": round(r["sweep_us"], 3),
+                        "bytes_per_node": r["bytes_per_node"],
+                        "hbm_frac": round(r["bytes_per_node"] * nodes / (r["sweep_us"] * 1e-6) / 1e9 / peak, 4),
+                        "mass_flow": r["mass_flow"], "clocks": r["clocks"]}
+    if "fp64" in results:
+        out["fp32s_over_fp64"] = round(results["fp32s"]["mlups"] / results["fp64"]["mlups"], 3)
     return out
 
 
@@ -317,15 +401,25 @@ def oracle_sample_run(nx_sample: int, steps: int, threads: int = 0):
     return dt, oracle.threads_used()
 
 
-def cpu_baseline(seconds: float = 15.0):
+def cpu_baseline(steps: int = 100):
     """The FP64 oracle as it stands, on all host cores, on a bounded sample:
-    full-length steps of the benchmark channel, as many as fit ~`seconds`."""
-    dt1, _ = oracle_sample_run(NX, 1)
-    steps = max(1, int(seconds / max(dt1, 1e-6)))
-    dt, cores = oracle_sample_run(NX, steps)
-    return {"value": round(NX * NY * steps / dt / 1e6, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+    `steps` time steps of the full benchmark channel.  Also returns the
+    oracle's state and observables for the error report."""
+    import oracle
+
+    p = oracle.OracleParams(nx=NX, ny=NY, pressure=True, kn=KN_OUT, rho_in=RATIO, rho_out=1.0)
+    s = oracle.OracleSim(p)
+    t0 = time.perf_counter()
+    s.step(steps, 0)
+    dt = time.perf_counter() - t0
+    cores = oracle.threads_used()
+    obs = s.observables()
+    ref = {"state": s.state(), "mass_flow": obs["mass_flow"], "dp_nonlin": obs["dp_nonlin"]}
+    s.close()
+    base = {"value": round(NX * NY * steps / dt / 1e6, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
             "sample": f"{steps} time steps of the full {NX}x{NY} channel from the initial state "
                       f"({dt:.1f} s, FP64, OpenMP over rows)"}
+    return base, ref
 
 
 def run_reference(args):
@@ -377,9 +471,12 @@ def main():
     ap.add_argument("--steps", type=int, default=10000)
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-steps", type=int, default=100,
+                    help="oracle steps of the CPU baseline (also the step count of the error report)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--variants", default="fp32s,fp64", help="storages to time (fp32s first)")
+    ap.add_argument("--variants", default="fp32s,fp64,fp16s,bf16s", help="storages to time (fp32s first)")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched Knudsen-sweep measurement")
+    ap.add_argument("--batch-steps", type=int, default=20000)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -59,8 +59,8 @@ typedef enum {
 typedef enum {
     CLB_FP64 = 0,         /* populations stored and collided in FP64 (144 B per node update) */
     CLB_FP32_SHIFTED = 1, /* FP32 deviations f - w_i rho_ref(x), FP32 collision (72 B) */
-    CLB_FP16_SCALED = 2,  /* reserved: 16-bit storage with a per-plane scale */
-    CLB_BF16_SCALED = 3   /* reserved */
+    CLB_FP16_SCALED = 2,  /* FP16 deviations times a field scale 2^14, FP32 collision (36 B) */
+    CLB_BF16_SCALED = 3   /* BF16 deviations (scale 1), FP32 collision (36 B) */
 } clb_storage;
 
 /* Optional settings; clb_opts_default() fills the paper's values (Sec. 3). */
@@ -70,7 +70,8 @@ typedef struct {
     double s3, s8;  /* free relaxation rates; 1.1, 1.2 */
     double rho_out; /* outlet density (pressure drive) or mean density (body force); 1.0 */
     int storage;    /* clb_storage; CLB_FP32_SHIFTED */
-    int vec;        /* nodes per thread along x (1, 2 or 4 for FP32, 1 or 2 for FP64); 0 = default */
+    int vec;        /* nodes per thread along x: FP64 1|2 (default 2), FP32 1|2|4 (4),
+                       16-bit 4|8 (4); 0 = default */
     int block_x;    /* threads per block, a multiple of 32 in 32..256; 0 = default 128 */
     void* stream;   /* cudaStream_t to queue work on; NULL = a stream owned by the library */
     /* Device allocator hooks (e.g. a framework's caching allocator); both NULL
@@ -170,6 +171,49 @@ clb_status clb_destroy(clb_sim* sim);
 
 /* Message for the last failing call on this thread ("" if none). */
 const char* clb_last_error(void);
+
+/* ------------------------------------------------------------------------
+ * Batched Knudsen sweep (Sec. 3.1, Fig. 2): many periodic body-force channels
+ * of uneven height and Knudsen number advanced together.  Each channel lives
+ * in the shared memory of one thread block for many steps (one persistent
+ * launch per chunk of steps, replayed from a CUDA graph), so the channel must
+ * fit: 9 * nx * ny * element size <= 200 KB.  Every channel uses the same a,
+ * r_b, G and opts (s3, s8, B2, sigma, rho_out); its rates s_v, s_q come from
+ * its own Kn and ny (Eq. 18, 21).  The arithmetic per node is that of
+ * clb_step on a periodic channel.
+ * ------------------------------------------------------------------------ */
+typedef struct clb_batch clb_batch; /* opaque */
+
+/* n channels; nx[k], ny[k], kn[k] per channel (host arrays).  opts->storage
+ * CLB_FP64 or CLB_FP32_SHIFTED; opts->block_x 0 = autotuned on the first
+ * clb_batch_step (or by clb_batch_tune), else threads per block (32..512).
+ * Initial state f^eq(rho_out, 0).  Errors: CLB_EINVAL, CLB_ENOMEM, CLB_ECUDA. */
+clb_status clb_batch_create(int n, const int* nx, const int* ny, const double* kn, double a, double r, double g,
+                            const clb_opts* opts, clb_batch** out);
+
+/* Advance every channel n >= 0 steps (queued on the batch's stream). */
+clb_status clb_batch_step(clb_batch* b, int64_t n);
+
+/* Time each candidate block size (64..512 threads) on a copy of the state and
+ * keep the fastest; the state itself does not advance.  Synchronises. */
+clb_status clb_batch_tune(clb_batch* b, int* block_x_out);
+
+/* Per-channel scalars into s[n] (mass_flow, q_norm = Q of Sec. 3.1, u_slip at
+ * column 0, total_mass, step; residual and ux_max are not computed: -1, 0).
+ * Synchronises.  CLB_ENUMERIC if a channel holds NaN/Inf. */
+clb_status clb_batch_observables(clb_batch* b, clb_scalars* s);
+
+/* Channel k's populations as FP64 host arrays [9][ny][nx] (layout of
+ * clb_get_state).  Synchronises; takes a transient device buffer. */
+clb_status clb_batch_get_state(clb_batch* b, int k, double* host_f);
+clb_status clb_batch_set_state(clb_batch* b, int k, const double* host_f);
+
+/* Block size in use, steps done, and the cudaStream_t (each may be NULL). */
+clb_status clb_batch_info(const clb_batch* b, int* block_x, int64_t* step, void** stream);
+
+/* Release everything; NULL is accepted. */
+clb_status clb_batch_destroy(clb_batch* b);
+
 
 /*
  * clb_observables_noalloc - the observables of clb_observables, computed from

@@ -13,6 +13,7 @@ from .clb import (  # noqa: F401
     CLB_FP32_SHIFTED,
     CLB_FP64,
     LIB_PATH,
+    Batch,
     Channel,
     CLBError,
     clb_create,

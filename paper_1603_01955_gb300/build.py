@@ -44,14 +44,19 @@ def stale() -> bool:
     return any(os.path.getmtime(p) > t for p in _deps())
 
 
-def build_library(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
-    if not force and not stale():
+def build_library(force: bool = False, verbose: bool = False, extra: list[str] | None = None,
+                  out: str | None = None) -> str:
+    """Compile and link; ``extra`` adds nvcc flags (e.g. -D build knobs) and
+    ``out`` writes the library elsewhere (default: the package's own)."""
+    target = out or LIB
+    if not force and out is None and not stale():
         return LIB
-    os.makedirs(BUILD, exist_ok=True)
+    build_dir = BUILD if out is None else out + ".objs"
+    os.makedirs(build_dir, exist_ok=True)
     procs = []
     objs = []
     for src in sources():
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         cmd = [nvcc(), *ARCH, *FLAGS, *(extra or []), "-c", src, "-o", obj]
         if verbose:
@@ -66,10 +71,10 @@ def build_library(force: bool = False, verbose: bool = False, extra: list[str] |
             failed.append(" ".join(cmd))
     if failed:
         raise RuntimeError("nvcc failed:\n" + "\n".join(failed))
-    tmp = LIB + ".tmp%d" % os.getpid()
+    tmp = target + ".tmp%d" % os.getpid()
     subprocess.run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs], check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, target)
+    return target
 
 
 if __name__ == "__main__":

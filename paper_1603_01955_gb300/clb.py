@@ -90,8 +90,20 @@ def _load():
     lib.clb_last_error.restype = C.c_char_p
     lib.clb_observables_noalloc.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
                                             C.c_double, C.c_int, P, C.POINTER(clb_scalars), D, D, D, D, D]
+    I = C.POINTER(C.c_int)
+    lib.clb_batch_create.argtypes = [C.c_int, I, I, D, C.c_double, C.c_double, C.c_double, C.POINTER(clb_opts),
+                                     C.POINTER(P)]
+    lib.clb_batch_step.argtypes = [P, C.c_int64]
+    lib.clb_batch_tune.argtypes = [P, I]
+    lib.clb_batch_observables.argtypes = [P, C.POINTER(clb_scalars)]
+    lib.clb_batch_get_state.argtypes = [P, C.c_int, P]
+    lib.clb_batch_set_state.argtypes = [P, C.c_int, P]
+    lib.clb_batch_info.argtypes = [P, I, C.POINTER(C.c_int64), C.POINTER(P)]
+    lib.clb_batch_destroy.argtypes = [P]
     for name in ("clb_create", "clb_step", "clb_observables", "clb_get_state", "clb_set_state",
-                 "clb_info", "clb_sync", "clb_destroy", "clb_observables_noalloc"):
+                 "clb_info", "clb_sync", "clb_destroy", "clb_observables_noalloc", "clb_batch_create",
+                 "clb_batch_step", "clb_batch_tune", "clb_batch_observables", "clb_batch_get_state",
+                 "clb_batch_set_state", "clb_batch_info", "clb_batch_destroy"):
         getattr(lib, name).restype = C.c_int
     return lib
 
@@ -178,6 +190,8 @@ class Channel:
     drive='body_force': periodic in x, ``drive_value`` = G (lattice acceleration).
     drive='pressure': inlet/outlet, ``drive_value`` = p_in/p_out, ``kn`` = Kn_out.
     ``r`` < 0 takes r_b from Eq. 21 with ``sigma``.
+    All work runs on ``self.stream`` (the given non-default torch stream, or a
+    new one); time it with events recorded on that stream.
     """
 
     def __init__(self, nx, ny, kn, a=2.0, r=-1.0, drive="body_force", drive_value=0.0, storage="fp32s",
@@ -187,7 +201,11 @@ class Channel:
 
         self.nx, self.ny = int(nx), int(ny)
         dev = torch.cuda.current_device()
-        self._stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        # a stream of its own by default; the legacy default stream (handle 0)
+        # cannot be handed over, because NULL asks the library for its own stream
+        if stream is None or stream.cuda_stream == 0:
+            stream = torch.cuda.Stream(dev)
+        self._stream = stream
         o = clb_opts_default()
         o.b2, o.sigma, o.s3, o.s8, o.rho_out = b2, sigma, s3, s8, rho_out
         o.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
@@ -261,3 +279,125 @@ class Channel:
         out = {k: getattr(s, k) for k, _ in clb_scalars._fields_}
         out.update(ux_prof=ux, uy_prof=uy, p_centre=pc, dp_nonlin=dp, m_of_x=mx, status=st)
         return out
+
+
+# ------------------------------------------------------------ batched sweep
+
+def clb_batch_create(nx, ny, kn, a, r, g, opts: clb_opts | None = None):
+    n = len(kn)
+    ax = (C.c_int * n)(*[int(v) for v in nx])
+    ay = (C.c_int * n)(*[int(v) for v in ny])
+    ak = (C.c_double * n)(*[float(v) for v in kn])
+    h = C.c_void_p()
+    _check(lib.clb_batch_create(n, ax, ay, ak, float(a), float(r), float(g),
+                                C.byref(opts) if opts is not None else None, C.byref(h)))
+    return h
+
+
+def clb_batch_step(b, n):
+    return _check(lib.clb_batch_step(b, int(n)))
+
+
+def clb_batch_tune(b):
+    blk = C.c_int()
+    _check(lib.clb_batch_tune(b, C.byref(blk)))
+    return blk.value
+
+
+def clb_batch_observables(b, n):
+    s = (clb_scalars * n)()
+    _check(lib.clb_batch_observables(b, s))
+    return s
+
+
+def clb_batch_get_state(b, k, host_ptr):
+    return _check(lib.clb_batch_get_state(b, int(k), C.c_void_p(host_ptr)))
+
+
+def clb_batch_set_state(b, k, host_ptr):
+    return _check(lib.clb_batch_set_state(b, int(k), C.c_void_p(host_ptr)))
+
+
+def clb_batch_info(b):
+    blk = C.c_int()
+    step = C.c_int64()
+    st = C.c_void_p()
+    _check(lib.clb_batch_info(b, C.byref(blk), C.byref(step), C.byref(st)))
+    return blk.value, step.value, st.value
+
+
+def clb_batch_destroy(b):
+    return _check(lib.clb_batch_destroy(b))
+
+
+class Batch:
+    """Many periodic body-force channels (the Knudsen sweep of Sec. 3.1) in one
+    persistent launch per chunk of steps, on its own torch stream."""
+
+    def __init__(self, nx, ny, kn, a=2.0, r=-1.0, g=1e-6, storage="fp32s", block_x=0, b2=0.55, sigma=1.0,
+                 s3=1.1, s8=1.2, rho_out=1.0, stream=None, torch_allocator=True):
+        import torch
+
+        self.nx, self.ny, self.kn = list(nx), list(ny), list(kn)
+        self.n = len(self.kn)
+        dev = torch.cuda.current_device()
+        if stream is None or stream.cuda_stream == 0:
+            stream = torch.cuda.Stream(dev)
+        self._stream = stream
+        o = clb_opts_default()
+        o.b2, o.sigma, o.s3, o.s8, o.rho_out = b2, sigma, s3, s8, rho_out
+        o.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+        o.block_x = int(block_x)
+        o.stream = C.c_void_p(stream.cuda_stream)
+        if torch_allocator:
+            def _alloc(nbytes, ctx):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream)
+                except Exception:  # noqa: BLE001 - reported to the library as NULL
+                    return None
+
+            def _free(p, ctx):
+                torch.cuda.caching_allocator_delete(int(p))
+
+            self._hooks = (ALLOC_FN(_alloc), FREE_FN(_free))
+            o.alloc, o.free = self._hooks
+        self.b = clb_batch_create(self.nx, self.ny, self.kn, a, r, g, o)
+
+    @property
+    def stream(self):
+        return self._stream
+
+    def close(self):
+        if getattr(self, "b", None):
+            clb_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def step(self, n=1):
+        clb_batch_step(self.b, n)
+
+    def tune(self):
+        return clb_batch_tune(self.b)
+
+    def info(self):
+        blk, step, _ = clb_batch_info(self.b)
+        return {"block_x": blk, "step": step}
+
+    def observables(self):
+        s = clb_batch_observables(self.b, self.n)
+        return [{k: getattr(x, k) for k, _ in clb_scalars._fields_} for x in s]
+
+    def state(self, k):
+        f = np.empty((9, self.ny[k], self.nx[k]), np.float64)
+        clb_batch_get_state(self.b, k, f.ctypes.data)
+        return f
+
+    def set_state(self, k, f):
+        f = np.ascontiguousarray(f, dtype=np.float64).reshape(9, self.ny[k], self.nx[k])
+        clb_batch_set_state(self.b, k, f.ctypes.data)
+

@@ -1,0 +1,555 @@
+// Batched Knudsen sweep: many small periodic channels (Sec. 3.1, Fig. 2 of
+// Liu & He, arXiv:1603.01955) advanced together by one persistent launch.
+//
+// Each channel (at most a few hundred nodes: Nx = 4 columns, Ny <= ~256 rows)
+// lives for the whole launch in the shared memory of one thread block, which
+// runs many time steps with only block barriers between them: gather the
+// pulled populations into registers (Eq. 5, CBBSR walls Eq. 20, periodic x),
+// barrier, collide (Eq. 4, 6-13 with the channel's own s_v, s_q from Eq. 18,
+// 21) and write back in place, barrier.  Global memory is touched once at
+// the start and once at the end of a launch.  The host replays a CUDA graph
+// holding one such launch of a fixed number of steps; an autotuner picks the
+// block size (and with it the nodes per thread) by timing the candidates on a
+// copy of the state.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/clb.h"
+#include "clb_device.cuh"
+#include "clb_internal.h"
+
+using namespace clb;
+
+namespace {
+
+struct BatchChannel {
+    int nx, ny;
+    long long offset;  // element offset of the channel's [9][ny][nx] block
+};
+
+struct BatchArgs {
+    void* state;
+    const BatchChannel* ch;
+    const KC<float>* kf;   // per-channel constants
+    const KC<double>* kd;
+};
+
+template <typename R> __device__ __forceinline__ const KC<R>* kcs(const BatchArgs& a);
+template <> __device__ __forceinline__ const KC<float>* kcs<float>(const BatchArgs& a) { return a.kf; }
+template <> __device__ __forceinline__ const KC<double>* kcs<double>(const BatchArgs& a) { return a.kd; }
+
+// Pre-collision populations of node (x, y) of a channel held in shared memory
+// as s[i][y][x], nx columns periodic, walls below row 0 and above row ny-1.
+template <class R>
+__device__ __forceinline__ void gather(const R* s, int nx, int ny, int x, int y, R r, R rc, R (&f)[9]) {
+    const int nn = nx * ny;
+    const int xm = x == 0 ? nx - 1 : x - 1;
+    const int xp = x == nx - 1 ? 0 : x + 1;
+    auto at = [&](int i, int yy, int xx) -> R { return s[i * nn + yy * nx + xx]; };
+    f[0] = at(0, y, x);
+    f[1] = at(1, y, xm);
+    f[3] = at(3, y, xp);
+    if (y == 0) {  // Eq. 20
+        f[2] = at(4, 0, x);
+        f[5] = r * at(7, 0, x) + rc * at(8, 0, xm);
+        f[6] = r * at(8, 0, x) + rc * at(7, 0, xp);
+    } else {
+        f[2] = at(2, y - 1, x);
+        f[5] = at(5, y - 1, xm);
+        f[6] = at(6, y - 1, xp);
+    }
+    if (y == ny - 1) {  // mirror of Eq. 20
+        f[4] = at(2, y, x);
+        f[7] = r * at(5, y, x) + rc * at(6, y, xp);
+        f[8] = r * at(6, y, x) + rc * at(5, y, xm);
+    } else {
+        f[4] = at(4, y + 1, x);
+        f[7] = at(7, y + 1, xp);
+        f[8] = at(8, y + 1, xm);
+    }
+}
+
+template <class T, int NPT>
+__global__ void __launch_bounds__(512) batch_kernel(const BatchArgs a, int nsteps) {
+    using R = T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R* s = reinterpret_cast<R*>(smem_raw);
+    const BatchChannel ch = a.ch[blockIdx.x];
+    const KC<R> c = kcs<R>(a)[blockIdx.x];
+    const int nx = ch.nx, ny = ch.ny, nn = nx * ny;
+    T* g = static_cast<T*>(a.state) + ch.offset;
+    for (int k = threadIdx.x; k < 9 * nn; k += blockDim.x) s[k] = g[k];
+    const R r = c.r, rc = c.rc, ref = c.ref0;
+    __syncthreads();
+    for (int t = 0; t < nsteps; ++t) {
+        R f[NPT][9];
+#pragma unroll
+        for (int q = 0; q < NPT; ++q) {
+            const int node = threadIdx.x + q * blockDim.x;
+            if (node < nn) gather(s, nx, ny, node % nx, node / nx, r, rc, f[q]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < NPT; ++q) {
+            const int node = threadIdx.x + q * blockDim.x;
+            if (node < nn) {
+                collide<R, MODE_PERIODIC>(f[q], ref, c);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) s[i * nn + node] = f[q][i];
+            }
+        }
+        __syncthreads();
+    }
+    for (int k = threadIdx.x; k < 9 * nn; k += blockDim.x) g[k] = s[k];
+}
+
+// Per channel: mass flow (mean over x of sum_y rho u_x), sum of u_x (for Q),
+// total mass, a non-finite count, and u_x in the first two and last two rows
+// of column 0 (slip).  One block of kObsThreads per channel; FP64 sums in a
+// fixed order.
+constexpr int kObsThreads = 256;
+
+template <class T>
+__global__ void __launch_bounds__(kObsThreads) batch_obs_kernel(const BatchArgs a, double ref0, double gx, double* out) {
+    __shared__ double sh[4][kObsThreads];
+    const BatchChannel ch = a.ch[blockIdx.x];
+    const int nx = ch.nx, ny = ch.ny, nn = nx * ny;
+    const T* g = static_cast<const T*>(a.state) + ch.offset;
+    double v[4] = {0, 0, 0, 0};
+    double* o = out + 9 * blockIdx.x;
+    for (int node = threadIdx.x; node < nn; node += kObsThreads) {
+        double drho = 0, jx = 0;
+        for (int i = 0; i < 9; ++i) {
+            const double f = (double)g[i * nn + node];
+            drho += f;
+            jx += (i == 1 || i == 5 || i == 8) ? f : (i == 3 || i == 6 || i == 7) ? -f : 0.0;
+        }
+        const double rho = ref0 + drho;
+        const double ux = (jx - 0.5 * rho * gx) / rho;  // Eq. 13 from the post-collision state
+        if (!isfinite(rho) || !isfinite(ux)) v[3] += 1;
+        v[0] += rho * ux;
+        v[1] += ux;
+        v[2] += rho;
+        const int x = node % nx, y = node / nx;
+        if (x == 0) {
+            if (y == 0) o[4] = ux;
+            if (y == 1) o[5] = ux;
+            if (y == ny - 2) o[6] = ux;
+            if (y == ny - 1) o[7] = ux;
+        }
+    }
+    for (int k = 0; k < 4; ++k) sh[k][threadIdx.x] = v[k];
+    __syncthreads();
+    for (int w = kObsThreads / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int k = 0; k < 4; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 4; ++k) o[k] = sh[k][0];
+}
+
+template <class T>
+__global__ void batch_canon_kernel(void* state, long long offset, long long n, double* buf, double ref0,
+                                   int to_canonical, int nn) {
+    // w_i by direction i = idx / nn
+    const double w[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+    T* g = static_cast<T*>(state) + offset;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const double wr = w[idx / nn] * ref0;
+        if (to_canonical)
+            buf[idx] = wr + (double)g[idx];
+        else
+            g[idx] = T(buf[idx] - wr);
+    }
+}
+
+}  // namespace
+
+struct clb_batch {
+    int n = 0, storage = 0, block_x = 0;
+    bool tuned = false;
+    size_t elem = 0;
+    long long total = 0;  // elements of the state
+    size_t smem = 0;      // bytes of shared memory per block
+    int max_nodes = 0;
+    std::vector<BatchChannel> hch;
+    std::vector<double> kn;
+    std::vector<int> nx, ny;
+    void* state = nullptr;
+    BatchChannel* dch = nullptr;
+    KC<float>* dkf = nullptr;
+    KC<double>* dkd = nullptr;
+    double* dobs = nullptr;
+    double g = 0, ref0 = 0, rho0 = 1, r = 0;
+    int64_t step = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaGraphExec_t graph = nullptr;
+    int graph_steps = 0, graph_block = 0;
+    void* (*alloc)(size_t, void*) = nullptr;
+    void (*dealloc)(void*, void*) = nullptr;
+    void* alloc_ctx = nullptr;
+
+    void* dalloc(size_t bytes) {
+        if (alloc) return alloc(bytes ? bytes : 256, alloc_ctx);
+        void* p = nullptr;
+        if (cudaMalloc(&p, bytes ? bytes : 256) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return p;
+    }
+    void dfree(void* p) {
+        if (!p) return;
+        if (dealloc)
+            dealloc(p, alloc_ctx);
+        else
+            cudaFree(p);
+    }
+};
+
+namespace {
+
+constexpr int kGraphSteps = 500;  // time steps per persistent launch in the replayed graph
+
+int npt_for(int max_nodes, int block) { return (max_nodes + block - 1) / block; }
+
+template <class T>
+cudaError_t launch_batch(clb_batch* b, void* state, int block, int nsteps, cudaStream_t st) {
+    BatchArgs a{state, b->dch, b->dkf, b->dkd};
+    const int npt = npt_for(b->max_nodes, block);
+    dim3 grid(b->n), blk(block);
+    switch (npt) {
+        case 1: batch_kernel<T, 1><<<grid, blk, b->smem, st>>>(a, nsteps); break;
+        case 2: batch_kernel<T, 2><<<grid, blk, b->smem, st>>>(a, nsteps); break;
+        case 3:
+        case 4: batch_kernel<T, 4><<<grid, blk, b->smem, st>>>(a, nsteps); break;
+        case 5:
+        case 6:
+        case 7:
+        case 8: batch_kernel<T, 8><<<grid, blk, b->smem, st>>>(a, nsteps); break;
+        default: return cudaErrorInvalidConfiguration;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch(clb_batch* b, void* state, int block, int nsteps, cudaStream_t st) {
+    return b->storage == CLB_FP64 ? launch_batch<double>(b, state, block, nsteps, st)
+                                  : launch_batch<float>(b, state, block, nsteps, st);
+}
+
+template <class T> cudaError_t set_smem_limit(size_t bytes) {
+    cudaError_t e = cudaSuccess;
+    const void* ks[] = {(const void*)batch_kernel<T, 1>, (const void*)batch_kernel<T, 2>,
+                        (const void*)batch_kernel<T, 4>, (const void*)batch_kernel<T, 8>};
+    for (const void* k : ks) {
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e != cudaSuccess) break;
+    }
+    return e;
+}
+
+void drop_graph(clb_batch* b) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+}
+
+clb_status build_graph(clb_batch* b) {
+    drop_graph(b);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t le = launch(b, b->state, b->block_x, kGraphSteps, b->stream);
+        e = cudaStreamEndCapture(b->stream, &g);
+        if (e == cudaSuccess) e = le;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        b->graph = nullptr;
+        return (clb_status)set_error(CLB_ECUDA, "clb_batch: graph capture: %s", cudaGetErrorString(e));
+    }
+    b->graph_steps = kGraphSteps;
+    b->graph_block = b->block_x;
+    return CLB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+clb_status clb_batch_destroy(clb_batch* b) {
+    if (!b) return CLB_OK;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    drop_graph(b);
+    b->dfree(b->state);
+    b->dfree(b->dch);
+    b->dfree(b->dkf);
+    b->dfree(b->dkd);
+    b->dfree(b->dobs);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return CLB_OK;
+}
+
+clb_status clb_batch_create(int n, const int* nx, const int* ny, const double* kn, double a, double r, double g,
+                            const clb_opts* opts, clb_batch** out) {
+    if (!out) return (clb_status)set_error(CLB_EINVAL, "clb_batch_create: out is NULL");
+    *out = nullptr;
+    if (n < 1 || n > 65535 || !nx || !ny || !kn)
+        return (clb_status)set_error(CLB_EINVAL, "clb_batch_create: need 1..65535 channels and their sizes");
+    clb_opts o;
+    clb_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.storage != CLB_FP64 && o.storage != CLB_FP32_SHIFTED)
+        return (clb_status)set_error(CLB_EINVAL, "clb_batch_create: storage must be FP64 or FP32-shifted");
+    if (!(a >= 0) || !std::isfinite(g) || !std::isfinite(r) || r > 1 || !(o.rho_out > 0))
+        return (clb_status)set_error(CLB_EINVAL, "clb_batch_create: a, r, g or rho_out out of range");
+    if ((o.alloc == nullptr) != (o.free == nullptr))
+        return (clb_status)set_error(CLB_EINVAL, "clb_batch_create: alloc and free hooks must be given together");
+    const size_t elem = o.storage == CLB_FP64 ? 8 : 4;
+    int max_nodes = 0;
+    for (int k = 0; k < n; ++k) {
+        if (nx[k] < 1 || ny[k] < 1 || !(kn[k] > 0) || !std::isfinite(kn[k]))
+            return (clb_status)set_error(CLB_EINVAL, "clb_batch_create: channel %d: bad nx, ny or Kn", k);
+        max_nodes = std::max(max_nodes, nx[k] * ny[k]);
+    }
+    const size_t smem = (size_t)9 * max_nodes * elem;
+    if (smem > 200 * 1024 || max_nodes > 8 * 512)
+        return (clb_status)set_error(CLB_EINVAL,
+                                     "clb_batch_create: the largest channel (%d nodes) does not fit one block's "
+                                     "shared memory",
+                                     max_nodes);
+    if (o.block_x && (o.block_x < 32 || o.block_x > 512 || o.block_x % 32))
+        return (clb_status)set_error(CLB_EINVAL, "clb_batch_create: block_x must be a multiple of 32 in 32..512");
+
+    clb_batch* b = new (std::nothrow) clb_batch;
+    if (!b) return (clb_status)set_error(CLB_ENOMEM, "clb_batch_create: host allocation failed");
+    b->n = n;
+    b->storage = o.storage;
+    b->elem = elem;
+    b->smem = smem;
+    b->max_nodes = max_nodes;
+    b->alloc = o.alloc;
+    b->dealloc = o.free;
+    b->alloc_ctx = o.alloc_ctx;
+    b->g = g;
+    b->rho0 = o.rho_out;
+    b->ref0 = o.storage == CLB_FP64 ? 0.0 : o.rho_out;
+    b->r = r >= 0 ? r : r_from_sigma(o.sigma);
+    b->block_x = o.block_x ? o.block_x : std::min(512, ((max_nodes + 31) / 32) * 32);
+    b->tuned = o.block_x != 0;
+    long long off = 0;
+    std::vector<KC<float>> kf(n);
+    std::vector<KC<double>> kd(n);
+    for (int k = 0; k < n; ++k) {
+        b->nx.push_back(nx[k]);
+        b->ny.push_back(ny[k]);
+        b->kn.push_back(kn[k]);
+        BatchChannel c{nx[k], ny[k], off};
+        b->hch.push_back(c);
+        off += ((9LL * nx[k] * ny[k] + 3) / 4) * 4;  // 16-byte aligned blocks
+        SweepArgs sa{};
+        sa.s3 = o.s3;
+        sa.s8 = o.s8;
+        rates_at(kn[k], ny[k], a, o.b2, &sa.sv, &sa.sq);
+        sa.rate_A = 1.0;  // unused in the body-force collision
+        sa.r = b->r;
+        sa.gx = g;
+        sa.ref0 = b->ref0;
+        sa.store_scale = 1.0;
+        derive_constants(sa);
+        kf[k] = sa.kf;
+        kd[k] = sa.kd;
+    }
+    b->total = off;
+    if (o.stream) {
+        b->stream = static_cast<cudaStream_t>(o.stream);
+    } else if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) == cudaSuccess) {
+        b->own_stream = true;
+    } else {
+        cudaError_t e = cudaGetLastError();
+        delete b;
+        return (clb_status)set_error(CLB_ECUDA, "clb_batch_create: stream: %s", cudaGetErrorString(e));
+    }
+    b->state = b->dalloc(b->total * elem);
+    b->dch = static_cast<BatchChannel*>(b->dalloc(n * sizeof(BatchChannel)));
+    b->dkf = static_cast<KC<float>*>(b->dalloc(n * sizeof(KC<float>)));
+    b->dkd = static_cast<KC<double>*>(b->dalloc(n * sizeof(KC<double>)));
+    b->dobs = static_cast<double*>(b->dalloc(9 * (size_t)n * sizeof(double)));
+    if (!b->state || !b->dch || !b->dkf || !b->dkd || !b->dobs) {
+        clb_batch_destroy(b);
+        return (clb_status)set_error(CLB_ENOMEM, "clb_batch_create: device allocation failed");
+    }
+    cudaError_t e = cudaMemcpyAsync(b->dch, b->hch.data(), n * sizeof(BatchChannel), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->dkf, kf.data(), n * sizeof(KC<float>), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->dkd, kd.data(), n * sizeof(KC<double>), cudaMemcpyHostToDevice, b->stream);
+    // initial state f^eq(rho_out, 0) = w_i rho_out: zero deviations (FP32) or w_i rho_out (FP64)
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->state, 0, b->total * elem, b->stream);
+    if (e == cudaSuccess) e = b->storage == CLB_FP64 ? set_smem_limit<double>(smem) : set_smem_limit<float>(smem);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        clb_batch_destroy(b);
+        return (clb_status)set_error(CLB_ECUDA, "clb_batch_create: %s", cudaGetErrorString(e));
+    }
+    if (b->storage == CLB_FP64) {
+        const double w[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+        for (int k = 0; k < n; ++k) {
+            const int nn = nx[k] * ny[k];
+            std::vector<double> f((size_t)9 * nn);
+            for (int i = 0; i < 9; ++i)
+                for (int j = 0; j < nn; ++j) f[(size_t)i * nn + j] = w[i] * o.rho_out;
+            e = cudaMemcpy(static_cast<double*>(b->state) + b->hch[k].offset, f.data(), f.size() * sizeof(double),
+                           cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) break;
+        }
+        if (e != cudaSuccess) {
+            clb_batch_destroy(b);
+            return (clb_status)set_error(CLB_ECUDA, "clb_batch_create: init: %s", cudaGetErrorString(e));
+        }
+    }
+    *out = b;
+    return CLB_OK;
+}
+
+clb_status clb_batch_tune(clb_batch* b, int* block_out) {
+    if (!b) return (clb_status)set_error(CLB_EINVAL, "clb_batch_tune: batch is NULL");
+    // time every block size on a scratch copy of the state (results do not
+    // depend on it, only the speed does)
+    void* scratch = b->dalloc(b->total * b->elem);
+    if (!scratch) return (clb_status)set_error(CLB_ENOMEM, "clb_batch_tune: device allocation failed");
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int best_block = b->block_x;
+    cudaError_t err = cudaSuccess;
+    const int trial_steps = 200;
+    for (int block = 64; block <= 512 && err == cudaSuccess; block *= 2) {
+        if (npt_for(b->max_nodes, block) > 8) continue;
+        err = cudaMemcpyAsync(scratch, b->state, b->total * b->elem, cudaMemcpyDeviceToDevice, b->stream);
+        if (err == cudaSuccess) err = launch(b, scratch, block, 20, b->stream);  // warm-up
+        if (err == cudaSuccess) err = cudaEventRecord(e0, b->stream);
+        if (err == cudaSuccess) err = launch(b, scratch, block, trial_steps, b->stream);
+        if (err == cudaSuccess) err = cudaEventRecord(e1, b->stream);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        float ms = 0;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+        if (err == cudaSuccess && ms < best) {
+            best = ms;
+            best_block = block;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamSynchronize(b->stream);
+    b->dfree(scratch);
+    if (err != cudaSuccess) return (clb_status)set_error(CLB_ECUDA, "clb_batch_tune: %s", cudaGetErrorString(err));
+    b->block_x = best_block;
+    b->tuned = true;
+    if (block_out) *block_out = best_block;
+    return CLB_OK;
+}
+
+clb_status clb_batch_step(clb_batch* b, int64_t n) {
+    if (!b || n < 0) return (clb_status)set_error(CLB_EINVAL, "clb_batch_step: bad arguments");
+    if (!b->tuned) {
+        clb_status st = clb_batch_tune(b, nullptr);
+        if (st != CLB_OK) return st;
+    }
+    if (n >= kGraphSteps && (!b->graph || b->graph_block != b->block_x)) {
+        clb_status st = build_graph(b);
+        if (st != CLB_OK) return st;
+    }
+    int64_t left = n;
+    while (left >= kGraphSteps) {
+        cudaError_t e = cudaGraphLaunch(b->graph, b->stream);
+        if (e != cudaSuccess) return (clb_status)set_error(CLB_ECUDA, "clb_batch_step: graph: %s", cudaGetErrorString(e));
+        left -= kGraphSteps;
+    }
+    if (left > 0) {
+        cudaError_t e = launch(b, b->state, b->block_x, (int)left, b->stream);
+        if (e != cudaSuccess) return (clb_status)set_error(CLB_ECUDA, "clb_batch_step: %s", cudaGetErrorString(e));
+    }
+    b->step += n;
+    return CLB_OK;
+}
+
+clb_status clb_batch_observables(clb_batch* b, clb_scalars* s) {
+    if (!b || !s) return (clb_status)set_error(CLB_EINVAL, "clb_batch_observables: NULL argument");
+    BatchArgs a{b->state, b->dch, b->dkf, b->dkd};
+    if (b->storage == CLB_FP64)
+        batch_obs_kernel<double><<<b->n, kObsThreads, 0, b->stream>>>(a, b->ref0, b->g, b->dobs);
+    else
+        batch_obs_kernel<float><<<b->n, kObsThreads, 0, b->stream>>>(a, b->ref0, b->g, b->dobs);
+    std::vector<double> h(9 * (size_t)b->n);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h.data(), b->dobs, h.size() * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return (clb_status)set_error(CLB_ECUDA, "clb_batch_observables: %s", cudaGetErrorString(e));
+    int bad = 0;
+    for (int k = 0; k < b->n; ++k) {
+        const double* o = h.data() + 9 * k;
+        const int ny = b->ny[k], nx = b->nx[k];
+        clb_scalars& sc = s[k];
+        sc.mass_flow = o[0] / nx;
+        // Q of Sec. 3.1: sum_y u_x / (3 G ny^2 sqrt(1/6)), averaged over the columns
+        sc.q_norm = b->g != 0 ? (o[1] / nx) / (3.0 * b->g * (double)ny * ny * std::sqrt(1.0 / 6.0)) : 0.0;
+        sc.u_slip = ny >= 2 ? 0.5 * ((1.5 * o[4] - 0.5 * o[5]) + (1.5 * o[7] - 0.5 * o[6])) : o[4];
+        sc.residual = -1.0;
+        sc.total_mass = o[2];
+        sc.ux_max = 0.0;
+        sc.step = b->step;
+        bad += o[3] > 0;
+    }
+    if (bad) return (clb_status)set_error(CLB_ENUMERIC, "clb_batch_observables: %d channels hold NaN/Inf", bad);
+    return CLB_OK;
+}
+
+static clb_status batch_copy(clb_batch* b, int k, double* host, int to_host) {
+    if (!b || !host || k < 0 || k >= b->n) return (clb_status)set_error(CLB_EINVAL, "clb_batch state: bad arguments");
+    const int nn = b->nx[k] * b->ny[k];
+    const long long n = 9LL * nn;
+    double* tmp = static_cast<double*>(b->dalloc(n * sizeof(double)));
+    if (!tmp) return (clb_status)set_error(CLB_ENOMEM, "clb_batch state: device allocation failed");
+    cudaError_t e = cudaSuccess;
+    if (!to_host) e = cudaMemcpyAsync(tmp, host, n * sizeof(double), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) {
+        if (b->storage == CLB_FP64)
+            batch_canon_kernel<double><<<64, 256, 0, b->stream>>>(b->state, b->hch[k].offset, n, tmp, b->ref0, to_host,
+                                                                 nn);
+        else
+            batch_canon_kernel<float><<<64, 256, 0, b->stream>>>(b->state, b->hch[k].offset, n, tmp, b->ref0, to_host,
+                                                                nn);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && to_host) e = cudaMemcpyAsync(host, tmp, n * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    b->dfree(tmp);
+    if (e != cudaSuccess) return (clb_status)set_error(CLB_ECUDA, "clb_batch state: %s", cudaGetErrorString(e));
+    return CLB_OK;
+}
+
+clb_status clb_batch_get_state(clb_batch* b, int k, double* host_f) { return batch_copy(b, k, host_f, 1); }
+
+clb_status clb_batch_set_state(clb_batch* b, int k, const double* host_f) {
+    return batch_copy(b, k, const_cast<double*>(host_f), 0);
+}
+
+clb_status clb_batch_info(const clb_batch* b, int* block_x, int64_t* step, void** stream) {
+    if (!b) return (clb_status)set_error(CLB_EINVAL, "clb_batch_info: batch is NULL");
+    if (block_x) *block_x = b->block_x;
+    if (step) *step = b->step;
+    if (stream) *stream = b->stream;
+    return CLB_OK;
+}
+
+}  // extern "C"

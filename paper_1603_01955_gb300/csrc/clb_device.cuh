@@ -7,11 +7,39 @@
 // and FP32 keeps its precision; with R = 0 the same code is the plain form.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "clb_internal.h"
 
 namespace clb {
+
+// Storage element <-> compute value.  FP64 and FP32 store the deviation
+// itself; the 16-bit formats store it times a power-of-two field scale
+// (FP16: keeps the small deviations out of the subnormal range; BF16: 1) and
+// are decoded to FP32 for the collision.
+template <class T> struct Codec;
+template <> struct Codec<double> {
+    using R = double;
+    static __device__ __forceinline__ double dec(double v, double) { return v; }
+    static __device__ __forceinline__ double enc(double v, double) { return v; }
+};
+template <> struct Codec<float> {
+    using R = float;
+    static __device__ __forceinline__ float dec(float v, float) { return v; }
+    static __device__ __forceinline__ float enc(float v, float) { return v; }
+};
+template <> struct Codec<__half> {
+    using R = float;
+    static __device__ __forceinline__ float dec(__half v, float isc) { return __half2float(v) * isc; }
+    static __device__ __forceinline__ __half enc(float v, float sc) { return __float2half_rn(v * sc); }
+};
+template <> struct Codec<__nv_bfloat16> {
+    using R = float;
+    static __device__ __forceinline__ float dec(__nv_bfloat16 v, float isc) { return __bfloat162float(v) * isc; }
+    static __device__ __forceinline__ __nv_bfloat16 enc(float v, float sc) { return __float2bfloat16_rn(v * sc); }
+};
 
 // D2Q9 rest weights: Eq. 11 at u = 0 through the closed-form inverse of Eq. 10.
 template <typename R> struct Wt {

@@ -29,6 +29,7 @@ template <typename R> struct KC {
     R ref0, slope;    // deviation reference R(x) = ref0 + slope x
     R sha, shd;       // added to a value pulled from column x-1: -w slope (axis, diagonal)
     R drho_in, drho_out;
+    R sc, isc;        // storage scale of the 16-bit formats and its inverse (1 otherwise)
 };
 
 // Everything one sweep launch needs (passed by value as a kernel argument).
@@ -52,12 +53,22 @@ struct SweepArgs {
     // R(x) = ref0 + ref_slope * x (R = 0 for FP64 storage).
     double ref0, ref_slope;
     double drho_in, drho_out; // rho_in - R(0), rho_out - R(nx-1)
+    double store_scale;       // stored value = deviation * store_scale (16-bit formats)
     KC<float> kf;             // the constants above, derived, in FP32
     KC<double> kd;            // ... and in FP64
 };
 
 // Fill a.kf and a.kd from the double fields of a.
 void derive_constants(SweepArgs& a);
+
+// s_v (Eq. 18) and s_q (Eq. 21) at a Knudsen number, N = ny.
+void rates_at(double kn, int ny, double a, double b2, double* sv, double* sq);
+
+// r_b of Eq. 21 from the TMAC sigma, with B1 = 1 - 0.1817 sigma (Sec. 3).
+double r_from_sigma(double sigma);
+
+// Record a failure message for clb_last_error() and return st.
+int set_error(int st, const char* fmt, ...);
 
 // Launch one sweep.  storage: clb_storage value; mode: MODE_*; vec: nodes per
 // thread along x; block_x: threads per block.

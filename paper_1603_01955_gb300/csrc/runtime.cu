@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "../../include/clb.h"
+#include "clb_device.cuh"
 #include "clb_internal.h"
 
 using namespace clb;
@@ -89,6 +90,7 @@ struct clb_sim {
     double kn = 0, a = 0, r = 0, b2 = 0, sigma = 1, s3 = 0, s8 = 0, g = 0, rho_in = 1, rho_out = 1;
     double sv = 0, sq = 0;
     double ref0 = 0, ref_slope = 0;
+    double store_scale = 1;  // 16-bit formats: stored value = deviation * store_scale
     int64_t step = 0;
     bool have_prev = false;
     double prev_mass_flow = 0;
@@ -117,9 +119,11 @@ struct clb_sim {
 
 namespace {
 
+template <class T> using RT = typename Codec<T>::R;
+
 template <class T>
 __global__ void init_kernel(T* f, int nx, int ny, int pitch, int xoff, long long plane, double rho_a,
-                            double rho_slope, double ref0, double ref_slope, int periodic) {
+                            double rho_slope, double ref0, double ref_slope, int periodic, double sc) {
     const long long n = 9LL * ny * nx;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
          idx += (long long)gridDim.x * blockDim.x) {
@@ -127,19 +131,19 @@ __global__ void init_kernel(T* f, int nx, int ny, int pitch, int xoff, long long
         const int y = (int)((idx / nx) % ny);
         const int i = (int)(idx / ((long long)nx * ny));
         // f^eq(rho_init(x), u = 0) = w_i rho_init(x) (Eq. 11), stored as a deviation from w_i R(x)
-        const double v = c_w[i] * ((rho_a + rho_slope * x) - (ref0 + ref_slope * x));
+        const T v = Codec<T>::enc(RT<T>(c_w[i] * ((rho_a + rho_slope * x) - (ref0 + ref_slope * x))), RT<T>(sc));
         T* row = f + i * plane + (long long)y * pitch + xoff;
-        row[x] = T(v);
+        row[x] = v;
         if (periodic) {
-            if (x == 0 && c_ex[i] < 0) row[nx] = T(v);
-            if (x == nx - 1 && c_ex[i] > 0) row[-1] = T(v);
+            if (x == 0 && c_ex[i] < 0) row[nx] = v;
+            if (x == nx - 1 && c_ex[i] > 0) row[-1] = v;
         }
     }
 }
 
 template <class T>
 __global__ void to_canonical_kernel(const T* f, double* out, int nx, int ny, int pitch, int xoff, long long plane,
-                                    double ref0, double ref_slope) {
+                                    double ref0, double ref_slope, double isc) {
     const long long n = 9LL * ny * nx;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
          idx += (long long)gridDim.x * blockDim.x) {
@@ -147,20 +151,20 @@ __global__ void to_canonical_kernel(const T* f, double* out, int nx, int ny, int
         const int y = (int)((idx / nx) % ny);
         const int i = (int)(idx / ((long long)nx * ny));
         const T* row = f + i * plane + (long long)y * pitch + xoff;
-        out[idx] = c_w[i] * (ref0 + ref_slope * x) + (double)row[x];
+        out[idx] = c_w[i] * (ref0 + ref_slope * x) + (double)Codec<T>::dec(row[x], RT<T>(isc));
     }
 }
 
 template <class T>
 __global__ void from_canonical_kernel(const double* in, T* f, int nx, int ny, int pitch, int xoff, long long plane,
-                                      double ref0, double ref_slope, int periodic) {
+                                      double ref0, double ref_slope, int periodic, double sc) {
     const long long n = 9LL * ny * nx;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
          idx += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(idx % nx);
         const int y = (int)((idx / nx) % ny);
         const int i = (int)(idx / ((long long)nx * ny));
-        const T v = T(in[idx] - c_w[i] * (ref0 + ref_slope * x));
+        const T v = Codec<T>::enc(RT<T>(in[idx] - c_w[i] * (ref0 + ref_slope * x)), RT<T>(sc));
         T* row = f + i * plane + (long long)y * pitch + xoff;
         row[x] = v;
         if (periodic) {
@@ -184,7 +188,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 template <class T>
 __global__ void __launch_bounds__(kObsCols* kObsRows)
     obs_kernel(const T* f, double* obs, ObsLayout L, int nx, int ny, int pitch, int xoff, long long plane,
-               double ref0, double ref_slope, double gx, double gy, int prof_col) {
+               double ref0, double ref_slope, double gx, double gy, int prof_col, double isc) {
     __shared__ double sh[5][kObsRows][kObsCols];
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int x = blockIdx.x * kObsCols + tx;
@@ -196,7 +200,7 @@ __global__ void __launch_bounds__(kObsCols* kObsRows)
             double drho = 0, jx = 0, jy = 0;
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
-                const double v = (double)row[i * plane];
+                const double v = (double)Codec<T>::dec(row[i * plane], RT<T>(isc));
                 drho += v;
                 jx += c_ex[i] * v;
                 jy += c_ey[i] * v;
@@ -267,6 +271,17 @@ __global__ void obs_final_kernel(double* obs, ObsLayout L) {
         for (int k = 0; k < 4; ++k) obs[L.part + k] = acc[k];
 }
 
+// Call f with a value of the storage element type.
+template <class F> cudaError_t with_storage(int storage, F&& f) {
+    switch (storage) {
+        case CLB_FP64: return f(double{});
+        case CLB_FP32_SHIFTED: return f(float{});
+        case CLB_FP16_SCALED: return f(__half{});
+        case CLB_BF16_SCALED: return f(__nv_bfloat16{});
+    }
+    return cudaErrorInvalidValue;
+}
+
 int grid_for(long long n, int block) {
     long long g = (n + block - 1) / block;
     return (int)std::min<long long>(std::max<long long>(g, 1), 152LL * 32);
@@ -299,9 +314,26 @@ SweepArgs make_args(const clb_sim* s) {
     a.ref_slope = s->ref_slope;
     a.drho_in = s->rho_in - s->ref_at(0);
     a.drho_out = s->rho_out - s->ref_at(s->nx - 1);
+    a.store_scale = s->store_scale;
     derive_constants(a);
     return a;
 }
+
+
+cudaError_t launch_init(clb_sim* s, void* buf, double rho_a, double rho_slope) {
+    const long long n = 9LL * s->nx * s->ny;
+    return with_storage(s->storage, [&](auto tag) {
+        using T = decltype(tag);
+        init_kernel<T><<<grid_for(n, 256), 256, 0, s->stream>>>(
+            static_cast<T*>(buf), s->nx, s->ny, s->pitch, s->xoff, s->plane, rho_a, rho_slope, s->ref0,
+            s->ref_slope, s->drive == CLB_DRIVE_BODY_FORCE, s->store_scale);
+        return cudaGetLastError();
+    });
+}
+
+}  // namespace
+
+namespace clb {
 
 void rates_at(double kn, int ny, double a, double b2, double* sv, double* sq) {
     // Eq. 18 and Eq. 21 (tau_q = 1/s_v - 1/2)
@@ -310,16 +342,20 @@ void rates_at(double kn, int ny, double a, double b2, double* sv, double* sq) {
     *sq = 1.0 / (0.5 + (3.0 + 4.0 * kPi * tau * tau * b2) / (16.0 * tau));
 }
 
-template <class T>
-cudaError_t launch_init(clb_sim* s, void* buf, double rho_a, double rho_slope) {
-    const long long n = 9LL * s->nx * s->ny;
-    init_kernel<T><<<grid_for(n, 256), 256, 0, s->stream>>>(
-        static_cast<T*>(buf), s->nx, s->ny, s->pitch, s->xoff, s->plane, rho_a, rho_slope, s->ref0, s->ref_slope,
-        s->drive == CLB_DRIVE_BODY_FORCE);
-    return cudaGetLastError();
+double r_from_sigma(double sigma) {
+    // Eq. 21 with sigma_v = (2 - sigma)/sigma (Eq. 19) and B1 = 1 - 0.1817 sigma
+    return 1.0 / (1.0 + (1.0 - 0.1817 * sigma) * (2.0 - sigma) / sigma * std::sqrt(kPi / 6.0));
 }
 
-}  // namespace
+int set_error(int st, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+}  // namespace clb
 
 // ---------------------------------------------------------------- C ABI
 
@@ -373,7 +409,7 @@ clb_status clb_create(int nx, int ny, double kn, double a, double r, clb_drive d
     if (!(o.rho_out > 0) || !(o.b2 >= 0) || !(o.s3 > 0 && o.s3 < 2) || !(o.s8 > 0 && o.s8 < 2))
         return fail(CLB_EINVAL, "clb_create: rho_out, b2, s3 or s8 out of range");
     if (r < 0 && !(o.sigma > 0 && o.sigma <= 2)) return fail(CLB_EINVAL, "clb_create: sigma must be in (0, 2]");
-    if (o.storage != CLB_FP64 && o.storage != CLB_FP32_SHIFTED)
+    if (o.storage < CLB_FP64 || o.storage > CLB_BF16_SCALED)
         return fail(CLB_EINVAL, "clb_create: storage %d not available", o.storage);
     if ((o.alloc == nullptr) != (o.free == nullptr))
         return fail(CLB_EINVAL, "clb_create: alloc and free hooks must be given together");
@@ -408,8 +444,7 @@ clb_status clb_create(int nx, int ny, double kn, double a, double r, clb_drive d
         s->g = 0;
         s->rho_in = drive_value * o.rho_out;
     }
-    // Eq. 21 with sigma_v = (2 - sigma)/sigma and B1 = 1 - 0.1817 sigma (Sec. 3)
-    s->r = r >= 0 ? r : 1.0 / (1.0 + (1.0 - 0.1817 * o.sigma) * (2.0 - o.sigma) / o.sigma * std::sqrt(kPi / 6.0));
+    s->r = r >= 0 ? r : r_from_sigma(o.sigma);
     rates_at(kn, ny, a, o.b2, &s->sv, &s->sq);
 
     // reference density of the stored deviations: the initial profile
@@ -424,7 +459,9 @@ clb_status clb_create(int nx, int ny, double kn, double a, double r, clb_drive d
         s->ref_slope = 0;
     }
 
-    s->elem = (o.storage == CLB_FP64) ? 8 : 4;
+    s->elem = (o.storage == CLB_FP64) ? 8 : (o.storage == CLB_FP32_SHIFTED) ? 4 : 2;
+    // FP16 keeps 2^-14 .. 4 in its normal range after this scale; BF16 has FP32's range
+    s->store_scale = (o.storage == CLB_FP16_SCALED) ? 16384.0 : 1.0;
     const int align = (int)(128 / s->elem);
     s->xoff = align;
     s->pitch = ((s->xoff + nx + 16 + align - 1) / align) * align;
@@ -475,10 +512,7 @@ clb_status clb_create(int nx, int ny, double kn, double a, double r, clb_drive d
     chk(cudaMemsetAsync(s->buf[1], 0, s->buf_bytes, s->stream), "memset");
     chk(cudaMemsetAsync(s->obs, 0, s->L.total * sizeof(double), s->stream), "memset");
     const double rho_slope = (drive == CLB_DRIVE_PRESSURE) ? (s->rho_out - s->rho_in) / (double)(nx - 1) : 0.0;
-    if (s->storage == CLB_FP64)
-        chk(launch_init<double>(s, s->buf[0], s->rho_in, rho_slope), "init");
-    else
-        chk(launch_init<float>(s, s->buf[0], s->rho_in, rho_slope), "init");
+    chk(launch_init(s, s->buf[0], s->rho_in, rho_slope), "init");
     chk(cudaStreamSynchronize(s->stream), "sync");
     if (st != CLB_OK) {
         clb_destroy(s);
@@ -539,15 +573,13 @@ clb_status clb_get_state(clb_sim* s, double* host_f) {
     double* tmp = static_cast<double*>(s->dalloc(n * sizeof(double)));
     if (!tmp) return fail(CLB_ENOMEM, "clb_get_state: device allocation failed");
     clb_status st = CLB_OK;
-    if (s->storage == CLB_FP64)
-        to_canonical_kernel<double><<<grid_for(n, 256), 256, 0, s->stream>>>(
-            static_cast<const double*>(s->buf[s->cur]), tmp, s->nx, s->ny, s->pitch, s->xoff, s->plane, s->ref0,
-            s->ref_slope);
-    else
-        to_canonical_kernel<float><<<grid_for(n, 256), 256, 0, s->stream>>>(
-            static_cast<const float*>(s->buf[s->cur]), tmp, s->nx, s->ny, s->pitch, s->xoff, s->plane, s->ref0,
-            s->ref_slope);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = with_storage(s->storage, [&](auto tag) {
+        using T = decltype(tag);
+        to_canonical_kernel<T><<<grid_for(n, 256), 256, 0, s->stream>>>(
+            static_cast<const T*>(s->buf[s->cur]), tmp, s->nx, s->ny, s->pitch, s->xoff, s->plane, s->ref0,
+            s->ref_slope, 1.0 / s->store_scale);
+        return cudaGetLastError();
+    });
     if (e == cudaSuccess) e = cudaMemcpyAsync(host_f, tmp, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) st = fail(CLB_ECUDA, "clb_get_state: %s", cudaGetErrorString(e));
@@ -564,15 +596,13 @@ clb_status clb_set_state(clb_sim* s, const double* host_f) {
     cudaError_t e = cudaMemcpyAsync(tmp, host_f, n * sizeof(double), cudaMemcpyHostToDevice, s->stream);
     const int periodic = s->drive == CLB_DRIVE_BODY_FORCE;
     if (e == cudaSuccess) {
-        if (s->storage == CLB_FP64)
-            from_canonical_kernel<double><<<grid_for(n, 256), 256, 0, s->stream>>>(
-                tmp, static_cast<double*>(s->buf[s->cur]), s->nx, s->ny, s->pitch, s->xoff, s->plane, s->ref0,
-                s->ref_slope, periodic);
-        else
-            from_canonical_kernel<float><<<grid_for(n, 256), 256, 0, s->stream>>>(
-                tmp, static_cast<float*>(s->buf[s->cur]), s->nx, s->ny, s->pitch, s->xoff, s->plane, s->ref0,
-                s->ref_slope, periodic);
-        e = cudaGetLastError();
+        e = with_storage(s->storage, [&](auto tag) {
+            using T = decltype(tag);
+            from_canonical_kernel<T><<<grid_for(n, 256), 256, 0, s->stream>>>(
+                tmp, static_cast<T*>(s->buf[s->cur]), s->nx, s->ny, s->pitch, s->xoff, s->plane, s->ref0,
+                s->ref_slope, periodic, s->store_scale);
+            return cudaGetLastError();
+        });
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) st = fail(CLB_ECUDA, "clb_set_state: %s", cudaGetErrorString(e));
@@ -589,15 +619,13 @@ clb_status clb_observables(clb_sim* s, int profile_col, clb_scalars* sc, double*
     const double gx = s->drive == CLB_DRIVE_BODY_FORCE ? s->g : 0.0;
     dim3 block(kObsCols, kObsRows);
     dim3 grid(s->L.nblocks);
-    if (s->storage == CLB_FP64)
-        obs_kernel<double><<<grid, block, 0, s->stream>>>(static_cast<const double*>(s->buf[s->cur]), s->obs, s->L,
-                                                         nx, ny, s->pitch, s->xoff, s->plane, s->ref0, s->ref_slope,
-                                                         gx, 0.0, profile_col);
-    else
-        obs_kernel<float><<<grid, block, 0, s->stream>>>(static_cast<const float*>(s->buf[s->cur]), s->obs, s->L, nx,
-                                                        ny, s->pitch, s->xoff, s->plane, s->ref0, s->ref_slope, gx,
-                                                        0.0, profile_col);
-    CUDA_OR(cudaGetLastError());
+    CUDA_OR(with_storage(s->storage, [&](auto tag) {
+        using T = decltype(tag);
+        obs_kernel<T><<<grid, block, 0, s->stream>>>(static_cast<const T*>(s->buf[s->cur]), s->obs, s->L, nx, ny,
+                                                    s->pitch, s->xoff, s->plane, s->ref0, s->ref_slope, gx, 0.0,
+                                                    profile_col, 1.0 / s->store_scale);
+        return cudaGetLastError();
+    }));
     obs_final_kernel<<<1, 32, 0, s->stream>>>(s->obs, s->L);
     CUDA_OR(cudaGetLastError());
     std::vector<double> h(s->L.part + 4);
@@ -716,7 +744,7 @@ extern "C" clb_status clb_observables_noalloc(const double* f_dev, int nx, int n
     CUDA_OR(cudaMemsetAsync(scratch, 0, L.total * sizeof(double), s));
     // populations in the canonical layout: row pitch nx, no halo, plain FP64 (R = 0)
     obs_kernel<double><<<dim3(L.nblocks), dim3(kObsCols, kObsRows), 0, s>>>(
-        f_dev, scratch, L, nx, ny, nx, 0, (long long)nx * ny, 0.0, 0.0, gx, 0.0, profile_col);
+        f_dev, scratch, L, nx, ny, nx, 0, (long long)nx * ny, 0.0, 0.0, gx, 0.0, profile_col, 1.0);
     CUDA_OR(cudaGetLastError());
     obs_final_kernel<<<1, 32, 0, s>>>(scratch, L);
     CUDA_OR(cudaGetLastError());

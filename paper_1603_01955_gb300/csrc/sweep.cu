@@ -28,9 +28,49 @@
 #include "clb_device.cuh"
 #include "clb_internal.h"
 
+// Build-time knobs (defaults: the measured best on GB300).
+// CLB_SWEEP_MIN_BLOCKS: resident 256-thread blocks per SM asked of the
+// compiler for the FP32/16-bit sweeps, which caps their registers: 4 -> 64
+// registers, 8 blocks of 128 threads per SM.  These kernels are bound by DRAM
+// latency, and the occupancy this buys outweighs a 36-byte spill.
+// CLB_SWEEP_MIN_BLOCKS_FP64: the same for the FP64 sweep (FP64-pipe bound).
+// CLB_SWEEP_STREAMING: 1 = evict-first (.cs) hints on the population loads
+// and stores, which are touched exactly once per step (measured slower).
+#ifndef CLB_SWEEP_MIN_BLOCKS
+#define CLB_SWEEP_MIN_BLOCKS 4
+#endif
+#ifndef CLB_SWEEP_MIN_BLOCKS_FP64
+#define CLB_SWEEP_MIN_BLOCKS_FP64 2
+#endif
+#ifndef CLB_SWEEP_STREAMING
+#define CLB_SWEEP_STREAMING 0
+#endif
+
 namespace clb {
 
+template <class T> struct MinBlocks { static constexpr int value = CLB_SWEEP_MIN_BLOCKS; };
+template <> struct MinBlocks<double> { static constexpr int value = CLB_SWEEP_MIN_BLOCKS_FP64; };
+
+template <class T> __device__ __forceinline__ T ld_stream(const T* p) {
+#if CLB_SWEEP_STREAMING
+    return __ldcs(p);
+#else
+    return __ldg(p);
+#endif
+}
+template <class T> __device__ __forceinline__ void st_stream(T* p, const T& v) {
+#if CLB_SWEEP_STREAMING
+    __stcs(p, v);
+#else
+    *p = v;
+#endif
+}
+
 template <class T, int V> struct Vec;
+template <> struct Vec<__half, 4> { using type = uint2; };
+template <> struct Vec<__half, 8> { using type = uint4; };
+template <> struct Vec<__nv_bfloat16, 4> { using type = uint2; };
+template <> struct Vec<__nv_bfloat16, 8> { using type = uint4; };
 template <> struct Vec<float, 1> { using type = float; };
 template <> struct Vec<float, 2> { using type = float2; };
 template <> struct Vec<float, 4> { using type = float4; };
@@ -40,7 +80,7 @@ template <> struct Vec<double, 2> { using type = double2; };
 template <class T, int V>
 __device__ __forceinline__ void vload(const T* p, T (&v)[V]) {
     using VT = typename Vec<T, V>::type;
-    const VT w = __ldg(reinterpret_cast<const VT*>(p));
+    const VT w = ld_stream(reinterpret_cast<const VT*>(p));
     const T* e = reinterpret_cast<const T*>(&w);
 #pragma unroll
     for (int k = 0; k < V; ++k) v[k] = e[k];
@@ -53,29 +93,30 @@ __device__ __forceinline__ void vstore(T* p, const T (&v)[V]) {
     T* e = reinterpret_cast<T*>(&w);
 #pragma unroll
     for (int k = 0; k < V; ++k) e[k] = v[k];
-    *reinterpret_cast<VT*>(p) = w;
+    st_stream(reinterpret_cast<VT*>(p), w);
 }
 
-// V columns x0..x0+V-1 of one row (zeros for threads past the halo column).
+// V columns x0..x0+V-1 of one row, decoded (zeros for threads past the halo
+// column).
 template <class T, class R, int V>
-__device__ __forceinline__ void row_vec(const T* row, int x0, bool live, R (&o)[V]) {
-    T v[V];
+__device__ __forceinline__ void row_vec(const T* row, int x0, bool live, R isc, R (&o)[V]) {
     if (live) {
+        T v[V];
         vload<T, V>(row + x0, v);
+#pragma unroll
+        for (int k = 0; k < V; ++k) o[k] = Codec<T>::dec(v[k], isc);
     } else {
 #pragma unroll
-        for (int k = 0; k < V; ++k) v[k] = T(0);
+        for (int k = 0; k < V; ++k) o[k] = R(0);
     }
-#pragma unroll
-    for (int k = 0; k < V; ++k) o[k] = R(v[k]);
 }
 
 // Columns x0-1..x0+V-2 from the vector of columns x0..x0+V-1 (a population
 // moving in +x): the first element comes from the previous lane.
 template <class T, class R, int V>
-__device__ __forceinline__ void from_left(const R (&v)[V], const T* row, int x0, int lane, R (&o)[V]) {
+__device__ __forceinline__ void from_left(const R (&v)[V], const T* row, int x0, int lane, R isc, R (&o)[V]) {
     R prev = __shfl_up_sync(0xffffffffu, v[V - 1], 1);
-    if (lane == 0) prev = R(__ldg(row + x0 - 1));
+    if (lane == 0) prev = Codec<T>::dec(__ldg(row + x0 - 1), isc);
     o[0] = prev;
 #pragma unroll
     for (int k = 1; k < V; ++k) o[k] = v[k - 1];
@@ -84,10 +125,10 @@ __device__ __forceinline__ void from_left(const R (&v)[V], const T* row, int x0,
 // Columns x0+1..x0+V (a population moving in -x): the last element comes from
 // the next lane.
 template <class T, class R, int V>
-__device__ __forceinline__ void from_right(const R (&v)[V], const T* row, int x0, int lane, bool live,
+__device__ __forceinline__ void from_right(const R (&v)[V], const T* row, int x0, int lane, bool live, R isc,
                                            R (&o)[V]) {
     R next = __shfl_down_sync(0xffffffffu, v[0], 1);
-    if (lane == 31 && live) next = R(__ldg(row + x0 + V));
+    if (lane == 31 && live) next = Codec<T>::dec(__ldg(row + x0 + V), isc);
 #pragma unroll
     for (int k = 0; k < V - 1; ++k) o[k] = v[k + 1];
     o[V - 1] = next;
@@ -105,7 +146,9 @@ template <class T, class R>
 __device__ void gather_node(const SweepArgs& a, const KC<R>& c, const T* fin, int x, int y, R o[9]) {
     const long long P = a.plane;
     const T* row = fin + (long long)y * a.pitch + a.xoff;
-    auto at = [&](int i, int dy, int xx) -> R { return R(__ldg(row + i * P + (long long)dy * a.pitch + xx)); };
+    auto at = [&](int i, int dy, int xx) -> R {
+        return Codec<T>::dec(__ldg(row + i * P + (long long)dy * a.pitch + xx), c.isc);
+    };
     const int rt = a.row_type[y];
     const R sha = c.sha, shd = c.shd;  // source at x-1; the source at x+1 gets the negative
     o[0] = at(0, 0, x);
@@ -163,9 +206,9 @@ __device__ __forceinline__ void rebuild_column(const SweepArgs& a, const KC<R>& 
 }
 
 template <class T, int MODE, int V>
-__global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a) {
-    using R = typename std::conditional<std::is_same<T, double>::value, double, float>::type;
-    constexpr bool kShift = (MODE == MODE_PRESSURE) && !std::is_same<T, double>::value;
+__global__ void __launch_bounds__(256, MinBlocks<T>::value) sweep_kernel(const SweepArgs a) {
+    using R = typename Codec<T>::R;
+    constexpr bool kShift = (MODE == MODE_PRESSURE) && !std::is_same<T, double>::value;  // R(x) != 0
     const T* __restrict__ fin = static_cast<const T*>(a.fin);
     T* __restrict__ fout = static_cast<T*>(a.fout);
 
@@ -182,13 +225,13 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a) {
 
     R f[9][V];
     // rest population and the two that move along x only (Eq. 5)
-    row_vec<T, R, V>(row, x0, live, f[0]);
+    row_vec<T, R, V>(row, x0, live, c.isc, f[0]);
     {
         R v[V];
-        row_vec<T, R, V>(row + 1 * P, x0, live, v);
-        from_left<T, R, V>(v, row + 1 * P, x0, lane, f[1]);
-        row_vec<T, R, V>(row + 3 * P, x0, live, v);
-        from_right<T, R, V>(v, row + 3 * P, x0, lane, live, f[3]);
+        row_vec<T, R, V>(row + 1 * P, x0, live, c.isc, v);
+        from_left<T, R, V>(v, row + 1 * P, x0, lane, c.isc, f[1]);
+        row_vec<T, R, V>(row + 3 * P, x0, live, c.isc, v);
+        from_right<T, R, V>(v, row + 3 * P, x0, lane, live, c.isc, f[3]);
         if (kShift) {
             add_shift<R, V>(f[1], c.sha);
             add_shift<R, V>(f[3], -c.sha);
@@ -198,11 +241,11 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a) {
     if (rt & ROW_BOTTOM) {
         // Eq. 20: fbar2 = f~4, fbar5 = r f~7 + (1-r) f~8(x-1), fbar6 = r f~8 + (1-r) f~7(x+1)
         R v4[V], v7[V], v8[V], s8[V], s7[V];
-        row_vec<T, R, V>(row + 4 * P, x0, live, v4);
-        row_vec<T, R, V>(row + 7 * P, x0, live, v7);
-        row_vec<T, R, V>(row + 8 * P, x0, live, v8);
-        from_left<T, R, V>(v8, row + 8 * P, x0, lane, s8);
-        from_right<T, R, V>(v7, row + 7 * P, x0, lane, live, s7);
+        row_vec<T, R, V>(row + 4 * P, x0, live, c.isc, v4);
+        row_vec<T, R, V>(row + 7 * P, x0, live, c.isc, v7);
+        row_vec<T, R, V>(row + 8 * P, x0, live, c.isc, v8);
+        from_left<T, R, V>(v8, row + 8 * P, x0, lane, c.isc, s8);
+        from_right<T, R, V>(v7, row + 7 * P, x0, lane, live, c.isc, s7);
         if (kShift) {
             add_shift<R, V>(s8, c.shd);
             add_shift<R, V>(s7, -c.shd);
@@ -216,11 +259,11 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a) {
     } else {
         const T* rd = row - a.pitch;
         R v[V];
-        row_vec<T, R, V>(rd + 2 * P, x0, live, f[2]);
-        row_vec<T, R, V>(rd + 5 * P, x0, live, v);
-        from_left<T, R, V>(v, rd + 5 * P, x0, lane, f[5]);
-        row_vec<T, R, V>(rd + 6 * P, x0, live, v);
-        from_right<T, R, V>(v, rd + 6 * P, x0, lane, live, f[6]);
+        row_vec<T, R, V>(rd + 2 * P, x0, live, c.isc, f[2]);
+        row_vec<T, R, V>(rd + 5 * P, x0, live, c.isc, v);
+        from_left<T, R, V>(v, rd + 5 * P, x0, lane, c.isc, f[5]);
+        row_vec<T, R, V>(rd + 6 * P, x0, live, c.isc, v);
+        from_right<T, R, V>(v, rd + 6 * P, x0, lane, live, c.isc, f[6]);
         if (kShift) {
             add_shift<R, V>(f[5], c.shd);
             add_shift<R, V>(f[6], -c.shd);
@@ -230,11 +273,11 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a) {
     if (rt & ROW_TOP) {
         // mirror of Eq. 20: fbar4 = f~2, fbar7 = r f~5 + (1-r) f~6(x+1), fbar8 = r f~6 + (1-r) f~5(x-1)
         R v2[V], v5[V], v6[V], s6[V], s5[V];
-        row_vec<T, R, V>(row + 2 * P, x0, live, v2);
-        row_vec<T, R, V>(row + 5 * P, x0, live, v5);
-        row_vec<T, R, V>(row + 6 * P, x0, live, v6);
-        from_right<T, R, V>(v6, row + 6 * P, x0, lane, live, s6);
-        from_left<T, R, V>(v5, row + 5 * P, x0, lane, s5);
+        row_vec<T, R, V>(row + 2 * P, x0, live, c.isc, v2);
+        row_vec<T, R, V>(row + 5 * P, x0, live, c.isc, v5);
+        row_vec<T, R, V>(row + 6 * P, x0, live, c.isc, v6);
+        from_right<T, R, V>(v6, row + 6 * P, x0, lane, live, c.isc, s6);
+        from_left<T, R, V>(v5, row + 5 * P, x0, lane, c.isc, s5);
         if (kShift) {
             add_shift<R, V>(s6, -c.shd);
             add_shift<R, V>(s5, c.shd);
@@ -248,11 +291,11 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a) {
     } else {
         const T* ru = row + a.pitch;
         R v[V];
-        row_vec<T, R, V>(ru + 4 * P, x0, live, f[4]);
-        row_vec<T, R, V>(ru + 7 * P, x0, live, v);
-        from_right<T, R, V>(v, ru + 7 * P, x0, lane, live, f[7]);
-        row_vec<T, R, V>(ru + 8 * P, x0, live, v);
-        from_left<T, R, V>(v, ru + 8 * P, x0, lane, f[8]);
+        row_vec<T, R, V>(ru + 4 * P, x0, live, c.isc, f[4]);
+        row_vec<T, R, V>(ru + 7 * P, x0, live, c.isc, v);
+        from_right<T, R, V>(v, ru + 7 * P, x0, lane, live, c.isc, f[7]);
+        row_vec<T, R, V>(ru + 8 * P, x0, live, c.isc, v);
+        from_left<T, R, V>(v, ru + 8 * P, x0, lane, c.isc, f[8]);
         if (kShift) {
             add_shift<R, V>(f[7], -c.shd);
             add_shift<R, V>(f[8], c.shd);
@@ -310,7 +353,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a) {
         for (int i = 0; i < 9; ++i) {
             T v[V];
 #pragma unroll
-            for (int k = 0; k < V; ++k) v[k] = T(f[i][k]);
+            for (int k = 0; k < V; ++k) v[k] = Codec<T>::enc(f[i][k], c.sc);
             vstore<T, V>(orow + i * P + x0, v);
         }
     } else {
@@ -318,7 +361,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a) {
         for (int k = 0; k < V; ++k)
             if (x0 + k < a.nx)
 #pragma unroll
-                for (int i = 0; i < 9; ++i) orow[i * P + x0 + k] = T(f[i][k]);
+                for (int i = 0; i < 9; ++i) orow[i * P + x0 + k] = Codec<T>::enc(f[i][k], c.sc);
     }
     if (MODE == MODE_PERIODIC) {
         // periodic images for the next sweep: column 0 -> halo column nx
@@ -326,14 +369,14 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a) {
 #pragma unroll
         for (int k = 0; k < V; ++k) {
             if (ct[k] & COL_HALO_RIGHT) {
-                orow[3 * P + a.nx] = T(f[3][k]);
-                orow[6 * P + a.nx] = T(f[6][k]);
-                orow[7 * P + a.nx] = T(f[7][k]);
+                orow[3 * P + a.nx] = Codec<T>::enc(f[3][k], c.sc);
+                orow[6 * P + a.nx] = Codec<T>::enc(f[6][k], c.sc);
+                orow[7 * P + a.nx] = Codec<T>::enc(f[7][k], c.sc);
             }
             if (ct[k] & COL_HALO_LEFT) {
-                orow[1 * P - 1] = T(f[1][k]);
-                orow[5 * P - 1] = T(f[5][k]);
-                orow[8 * P - 1] = T(f[8][k]);
+                orow[1 * P - 1] = Codec<T>::enc(f[1][k], c.sc);
+                orow[5 * P - 1] = Codec<T>::enc(f[5][k], c.sc);
+                orow[8 * P - 1] = Codec<T>::enc(f[8][k], c.sc);
             }
         }
     }
@@ -375,6 +418,8 @@ template <typename R> static void fill(KC<R>& c, const SweepArgs& a) {
     c.shd = R(-a.ref_slope / 36.0);
     c.drho_in = R(a.drho_in);
     c.drho_out = R(a.drho_out);
+    c.sc = R(a.store_scale);
+    c.isc = R(1.0 / a.store_scale);
 }
 
 void derive_constants(SweepArgs& a) {
@@ -385,6 +430,7 @@ void derive_constants(SweepArgs& a) {
 bool sweep_supported(int storage, int vec) {
     if (storage == 0) return vec == 1 || vec == 2;
     if (storage == 1) return vec == 1 || vec == 2 || vec == 4;
+    if (storage == 2 || storage == 3) return vec == 4 || vec == 8;
     return false;
 }
 
@@ -396,6 +442,12 @@ cudaError_t launch_sweep(int storage, int mode, int vec, int block_x, const Swee
         if (vec == 1) return launch_mode<float, 1>(mode, block_x, a, s);
         if (vec == 2) return launch_mode<float, 2>(mode, block_x, a, s);
         if (vec == 4) return launch_mode<float, 4>(mode, block_x, a, s);
+    } else if (storage == 2) {
+        if (vec == 4) return launch_mode<__half, 4>(mode, block_x, a, s);
+        if (vec == 8) return launch_mode<__half, 8>(mode, block_x, a, s);
+    } else if (storage == 3) {
+        if (vec == 4) return launch_mode<__nv_bfloat16, 4>(mode, block_x, a, s);
+        if (vec == 8) return launch_mode<__nv_bfloat16, 8>(mode, block_x, a, s);
     }
     return cudaErrorInvalidValue;
 }

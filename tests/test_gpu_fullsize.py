@@ -100,3 +100,20 @@ def test_full_size_short_run(clb, oracle_mod):
     assert g32["mass_flow"] == pytest.approx(o["mass_flow"], rel=1e-5)
     assert np.abs(g32["m_of_x"] - o["m_of_x"]).max() <= 1e-5 * np.abs(o["m_of_x"]).max()
     assert g32["total_mass"] == pytest.approx(o["total_mass"], rel=1e-9)
+
+
+@pytest.mark.parametrize("storage,eps", [("fp16s", 2.0**-11), ("bf16s", 2.0**-8)])
+def test_full_size_one_step_sampled_16bit(clb, oracle_mod, storage, eps):
+    nx, ny = C3["nx"], C3["ny"]
+    ch = clb.Channel(nx, ny, C3["kn_out"], drive="pressure", drive_value=C3["ratio"], storage=storage)
+    ch.step(60)
+    f0 = ch.state()
+    ch.step(1)
+    f1 = ch.state()
+    xs, ys = sample_nodes(nx, ny)
+    want = oracle_mod.step_nodes(params(oracle_mod), f0, xs, ys)
+    got = f1[:, ys, xs].T
+    w = oracle_mod.feq(1.0, 0.0, 0.0)
+    dev = want - w[None, :] * reference_profile(nx)[xs][:, None]
+    # one rounding of the stored output (half an ulp) plus the FP32 collision
+    assert np.abs(got - want).max() <= eps * np.abs(dev).max() + 8 * 2.0**-24 * np.abs(dev).max()

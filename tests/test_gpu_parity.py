@@ -247,3 +247,48 @@ def test_fp32_random_states(clb, oracle_mod, seed):
     assert np.abs(ch.state() - so).max() <= tol32(200) * scale
     nodes = nx * ny
     assert abs(ch.observables()["total_mass"] - orc.observables()["total_mass"]) <= nodes * rho_bound(200, scale)
+
+
+# ------------------------------------------------------------ 16-bit parity
+#
+# FP16 (x 2^14) and BF16 store the deviations with unit round-off 2^-11 and
+# 2^-8; the collision runs in FP32.  Same error model as FP32 with that
+# round-off: c * eps * sqrt(n) * max|d| per population, c = 4; the mass flow
+# (a sum of six populations per node) within 6x that per node.
+
+EPS16 = {"fp16s": 2.0**-11, "bf16s": 2.0**-8}
+
+
+def tol16(storage, n):
+    return 4 * EPS16[storage] * np.sqrt(max(n, 1))
+
+
+@pytest.mark.parametrize("storage", ["fp16s", "bf16s"])
+@pytest.mark.parametrize("kn_out", [0.0194, 0.2])
+def test_16bit_pressure_channel_1601x16_1000_steps(clb, oracle_mod, storage, kn_out):
+    c = inputs.PRESSURE_1601x16
+    ch, orc = pair(clb, oracle_mod, c["nx"], c["ny"], kn_out, "pressure", c["ratio"], storage=storage)
+    ch.step(1000)
+    orc.step(1000)
+    so = orc.state()
+    scale = dev_scale(so, oracle_mod, "pressure", c["ratio"])
+    err = np.abs(ch.state() - so).max()
+    assert err <= tol16(storage, 1000) * scale
+    g, o = ch.observables(), orc.observables()
+    assert abs(g["mass_flow"] - o["mass_flow"]) <= 6 * c["ny"] * tol16(storage, 1000) * scale
+
+
+@pytest.mark.parametrize("storage", ["fp16s", "bf16s"])
+@pytest.mark.parametrize("nx,ny,drive,vec", [(5, 3, "body_force", 4), (37, 4, "body_force", 8),
+                                             (4, 2, "pressure", 4), (131, 5, "pressure", 8)])
+def test_16bit_edge_sizes(clb, oracle_mod, storage, nx, ny, drive, vec):
+    value = 1.7 if drive == "pressure" else 3e-4
+    ch, orc = pair(clb, oracle_mod, nx, ny, 0.3, drive, value, storage=storage, vec=vec, block_x=32)
+    f0 = inputs.perturb(inputs.rng(nx + ny), orc.state(), 0.1)
+    ch.set_state(f0)
+    orc.set_state(f0)
+    ch.step(100)
+    orc.step(100)
+    so = orc.state()
+    # the initial state itself is rounded to 16 bits: one more rounding step
+    assert np.abs(ch.state() - so).max() <= tol16(storage, 101) * dev_scale(so, oracle_mod, drive, value)
