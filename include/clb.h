@@ -214,6 +214,31 @@ clb_status clb_batch_info(const clb_batch* b, int* block_x, int64_t* step, void*
 /* Release everything; NULL is accepted. */
 clb_status clb_batch_destroy(clb_batch* b);
 
+/* ------------------------------------------------------------------------
+ * Discrete adjoint of a periodic body-force channel (Sec. 3.1): the gradient
+ * of the flow sum J = (1/nx) sum_{x,y} u_x after nsteps steps from
+ * f^eq(rho_out, 0) with respect to r_b (Eq. 20), the Bosanquet factor a
+ * (Eq. 16-18, 21: through s_v and s_q) and the body force G (Eq. 9, 13).
+ * The normalised flow rate of Sec. 3.1 is Q = J / (3 G ny^2 sqrt(1/6)).
+ * ------------------------------------------------------------------------ */
+typedef struct clb_adjoint clb_adjoint; /* opaque */
+
+/* Run the forward pass, keeping a checkpoint every checkpoint_every steps
+ * (<= 0: ceil(sqrt(nsteps))), and return J.  opts->storage CLB_FP64 or
+ * CLB_FP32_SHIFTED (states and adjoints in that precision; the parameter
+ * sums are FP64).  r < 0 takes r_b from Eq. 21 with opts->sigma (the gradient
+ * is still with respect to r_b).  Device memory: (ceil(nsteps/C) + C + 5)
+ * states of 9 nx ny elements.  Synchronises.  nx * ny <= 2^22. */
+clb_status clb_adjoint_forward(int nx, int ny, double kn, double a, double r, double g, int64_t nsteps,
+                               int checkpoint_every, const clb_opts* opts, clb_adjoint** out, double* J);
+
+/* grad[0..2] = seed * dJ/d(r_b, a, G), walking the checkpointed forward pass
+ * backwards (recomputing each segment).  May be called repeatedly.
+ * Synchronises. */
+clb_status clb_adjoint_backward(clb_adjoint* h, double seed, double grad[3]);
+
+/* Release everything; NULL is accepted. */
+clb_status clb_adjoint_destroy(clb_adjoint* h);
 
 /*
  * clb_observables_noalloc - the observables of clb_observables, computed from

@@ -16,6 +16,7 @@ from .clb import (  # noqa: F401
     Batch,
     Channel,
     CLBError,
+    FlowGradient,
     clb_create,
     clb_destroy,
     clb_get_state,
@@ -25,4 +26,5 @@ from .clb import (  # noqa: F401
     clb_set_state,
     clb_step,
     clb_sync,
+    flow_rate,
 )

@@ -100,10 +100,15 @@ def _load():
     lib.clb_batch_set_state.argtypes = [P, C.c_int, P]
     lib.clb_batch_info.argtypes = [P, I, C.POINTER(C.c_int64), C.POINTER(P)]
     lib.clb_batch_destroy.argtypes = [P]
+    lib.clb_adjoint_forward.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double,
+                                        C.c_int64, C.c_int, C.POINTER(clb_opts), C.POINTER(P), D]
+    lib.clb_adjoint_backward.argtypes = [P, C.c_double, D]
+    lib.clb_adjoint_destroy.argtypes = [P]
     for name in ("clb_create", "clb_step", "clb_observables", "clb_get_state", "clb_set_state",
                  "clb_info", "clb_sync", "clb_destroy", "clb_observables_noalloc", "clb_batch_create",
                  "clb_batch_step", "clb_batch_tune", "clb_batch_observables", "clb_batch_get_state",
-                 "clb_batch_set_state", "clb_batch_info", "clb_batch_destroy"):
+                 "clb_batch_set_state", "clb_batch_info", "clb_batch_destroy", "clb_adjoint_forward",
+                 "clb_adjoint_backward", "clb_adjoint_destroy"):
         getattr(lib, name).restype = C.c_int
     return lib
 
@@ -401,3 +406,112 @@ class Batch:
         f = np.ascontiguousarray(f, dtype=np.float64).reshape(9, self.ny[k], self.nx[k])
         clb_batch_set_state(self.b, k, f.ctypes.data)
 
+
+# ------------------------------------------------------------ adjoint
+
+def clb_adjoint_forward(nx, ny, kn, a, r, g, nsteps, checkpoint_every=0, opts: clb_opts | None = None):
+    h = C.c_void_p()
+    J = C.c_double()
+    _check(lib.clb_adjoint_forward(int(nx), int(ny), float(kn), float(a), float(r), float(g), int(nsteps),
+                                   int(checkpoint_every), C.byref(opts) if opts is not None else None,
+                                   C.byref(h), C.byref(J)))
+    return h, J.value
+
+
+def clb_adjoint_backward(h, seed=1.0):
+    grad = (C.c_double * 3)()
+    _check(lib.clb_adjoint_backward(h, float(seed), grad))
+    return list(grad)
+
+
+def clb_adjoint_destroy(h):
+    return _check(lib.clb_adjoint_destroy(h))
+
+
+class FlowGradient:
+    """J = mean_x sum_y u_x of a periodic body-force channel after nsteps, and
+    its adjoint gradient with respect to (r_b, a, G).  Q = J / (3 G ny^2
+    sqrt(1/6)) is the normalised flow rate of Sec. 3.1."""
+
+    def __init__(self, nx, ny, kn, a, r, g, nsteps, storage="fp32s", checkpoint_every=0, b2=0.55, sigma=1.0,
+                 s3=1.1, s8=1.2, rho_out=1.0, stream=None):
+        import torch
+
+        dev = torch.cuda.current_device()
+        if stream is None or stream.cuda_stream == 0:
+            stream = torch.cuda.Stream(dev)
+        self._stream = stream
+        o = clb_opts_default()
+        o.b2, o.sigma, o.s3, o.s8, o.rho_out = b2, sigma, s3, s8, rho_out
+        o.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+        o.stream = C.c_void_p(stream.cuda_stream)
+
+        def _alloc(nbytes, ctx):
+            try:
+                return torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream)
+            except Exception:  # noqa: BLE001 - reported to the library as NULL
+                return None
+
+        def _free(p, ctx):
+            torch.cuda.caching_allocator_delete(int(p))
+
+        self._hooks = (ALLOC_FN(_alloc), FREE_FN(_free))
+        o.alloc, o.free = self._hooks
+        self.ny, self.g = int(ny), float(g)
+        self.h, self.J = clb_adjoint_forward(nx, ny, kn, a, r, g, nsteps, checkpoint_every, o)
+
+    def grad(self, seed=1.0):
+        """seed * dJ/d(r_b, a, G)."""
+        return clb_adjoint_backward(self.h, seed)
+
+    @property
+    def q_norm(self):
+        return self.J / (3.0 * self.g * self.ny**2 * (1.0 / 6.0) ** 0.5)
+
+    def close(self):
+        if getattr(self, "h", None):
+            clb_adjoint_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+
+def _flow_rate_function():
+    import torch
+
+    class FlowRate(torch.autograd.Function):
+        """Q(r_b, a, G) of a periodic channel (Sec. 3.1) as a differentiable
+        torch op: the forward pass runs the channel with checkpoints, the
+        backward pass runs the hand-written adjoint kernels."""
+
+        @staticmethod
+        def forward(ctx, r, a, g, cfg):
+            fg = FlowGradient(cfg["nx"], cfg["ny"], cfg["kn"], float(a), float(r), float(g), cfg["nsteps"],
+                              storage=cfg.get("storage", "fp32s"), checkpoint_every=cfg.get("checkpoint_every", 0))
+            ctx.fg = fg
+            ctx.norm = 3.0 * float(g) * cfg["ny"] ** 2 * (1.0 / 6.0) ** 0.5
+            ctx.g = float(g)
+            return torch.tensor(fg.J / ctx.norm, dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, gout):
+            fg = ctx.fg
+            dr, da, dg = fg.grad(1.0)
+            q = fg.J / ctx.norm
+            fg.close()
+            s = float(gout)
+            grads = (dr / ctx.norm * s, da / ctx.norm * s, (dg / ctx.norm - q / ctx.g) * s)
+            return tuple(torch.tensor(v, dtype=torch.float64) for v in grads) + (None,)
+
+    return FlowRate
+
+
+def flow_rate(r, a, g, cfg):
+    """Differentiable normalised flow rate Q (see FlowRate); r, a, g are
+    0-dim float64 tensors, cfg = dict(nx, ny, kn, nsteps[, storage,
+    checkpoint_every])."""
+    return _flow_rate_function().apply(r, a, g, cfg)
