@@ -33,8 +33,11 @@
  *    f^neq carries no mass, so rho(0,y) = rho_in exactly.  (Extrapolating
  *    f^neq linearly too, 2 f^neq(1) - f^neq(2), amplifies the shortest
  *    x-wavelength threefold and diverges at the outlet once tau ~ 30.)
- *  - Local Knudsen number (Sec. 3.2): Kn = Kn_out p_out / p taken per node
- *    with p = rho/3 at that node.
+ *  - Local Knudsen number (Sec. 3.2): Kn = Kn_out p_out / p, with p = rho/3
+ *    taken per node (kn_mode 0), or, as the paper states it, from the
+ *    centreline pressure of the column (kn_mode 1: the middle row, or the mean
+ *    of the two middle rows, of the state before the step, i.e. one step
+ *    behind; identical at steady state).
  *  - tau~_q in Eq. 21 is 1/s_v - 1/2, as the sentence after Eq. 21 defines it.
  *  - Initial state: f~ = f^eq(rho_init(x), 0), rho_init = rho_out (periodic)
  *    or linear from rho_in at x = 0 to rho_out at x = nx-1 (pressure).
@@ -317,6 +320,7 @@ struct oracle_sim {
     oracle_params p;
     real_t* ft; /* post-collision state, [9][ny][nx] */
     real_t* fb; /* work: pre-collision populations */
+    real_t* rc; /* work: centreline density per column (kn_mode 1) */
     real_t sv_const, sq_const;
 };
 
@@ -326,6 +330,8 @@ int oracle_threads_used(void) { return g_threads_used; }
 
 #define IDX(i, y, x, nx, ny) ((((size_t)(i)) * (size_t)(ny) + (size_t)(y)) * (size_t)(nx) + (size_t)(x))
 
+/* rho: the density that sets the local Knudsen number (the node's own, or
+ * the column's centreline density in kn_mode 1). */
 static void node_rates(const oracle_params* p, real_t rho, real_t s[9])
 {
     real_t sv, sq;
@@ -350,6 +356,7 @@ oracle_sim* oracle_create(const oracle_params* p)
     const size_t n = (size_t)NQ * p->nx * p->ny;
     s->ft = (real_t*)malloc(n * sizeof(real_t));
     s->fb = (real_t*)malloc(n * sizeof(real_t));
+    s->rc = (real_t*)malloc((size_t)p->nx * sizeof(real_t));
     for (int x = 0; x < p->nx; ++x) {
         real_t rho0 = p->rho_out;
         if (p->pressure)
@@ -367,6 +374,7 @@ void oracle_destroy(oracle_sim* s)
     if (!s) return;
     free(s->ft);
     free(s->fb);
+    free(s->rc);
     free(s);
 }
 
@@ -487,7 +495,24 @@ static void stream_and_boundaries(const oracle_params* p, const real_t* ft, real
     }
 }
 
-static void collide_all(const oracle_params* p, const real_t* fb, real_t* ft, int nthreads)
+/* Centreline density of each column of a state: the middle row, or the mean
+ * of the two middle rows. */
+static void centreline_density(const oracle_params* p, const real_t* f, real_t* rc)
+{
+    const int nx = p->nx, ny = p->ny;
+    for (int x = 0; x < nx; ++x) {
+        real_t r0 = 0.0, r1 = 0.0;
+        const int y0 = (ny % 2) ? (ny - 1) / 2 : ny / 2 - 1;
+        const int y1 = (ny % 2) ? y0 : ny / 2;
+        for (int i = 0; i < NQ; ++i) {
+            r0 += f[IDX(i, y0, x, nx, ny)];
+            r1 += f[IDX(i, y1, x, nx, ny)];
+        }
+        rc[x] = (ny % 2) ? r0 : 0.5 * (r0 + r1);
+    }
+}
+
+static void collide_all(const oracle_params* p, const real_t* fb, real_t* ft, const real_t* rc, int nthreads)
 {
     const int nx = p->nx, ny = p->ny;
 #pragma omp parallel for num_threads(nthreads) schedule(static)
@@ -498,7 +523,7 @@ static void collide_all(const oracle_params* p, const real_t* fb, real_t* ft, in
         for (int x = 0; x < nx; ++x) {
             real_t f[9], o[9], s[9];
             for (int i = 0; i < NQ; ++i) f[i] = fb[IDX(i, y, x, nx, ny)];
-            node_rates(p, raw_moment(f, 0, 0), s);
+            node_rates(p, (p->pressure && p->kn_mode == 1) ? rc[x] : raw_moment(f, 0, 0), s);
             oracle_collide(f, P_gx(p), p->gy, s, o, NULL, NULL);
             for (int i = 0; i < NQ; ++i) ft[IDX(i, y, x, nx, ny)] = o[i];
         }
@@ -520,8 +545,9 @@ int64_t oracle_step(oracle_sim* s, int64_t nsteps, int nthreads)
     nthreads = resolve_threads(nthreads);
     g_threads_used = 1;
     for (int64_t t = 0; t < nsteps; ++t) {
+        centreline_density(&s->p, s->ft, s->rc); /* of the state before the step */
         stream_and_boundaries(&s->p, s->ft, s->fb, nthreads);
-        collide_all(&s->p, s->fb, s->ft, nthreads);
+        collide_all(&s->p, s->fb, s->ft, s->rc, nthreads);
     }
     return nsteps;
 }
@@ -561,10 +587,21 @@ void oracle_step_nodes(const oracle_params* p, const real_t* f_prev, int n, cons
                        const int* ys, real_t* out)
 {
     ensure_tables();
+    const int y0 = (p->ny % 2) ? (p->ny - 1) / 2 : p->ny / 2 - 1;
+    const int y1 = (p->ny % 2) ? y0 : p->ny / 2;
     for (int k = 0; k < n; ++k) {
         real_t fb[9], s[9];
         arrive(p, f_prev, xs[k], ys[k], fb);
-        node_rates(p, raw_moment(fb, 0, 0), s);
+        real_t rho_kn = raw_moment(fb, 0, 0);
+        if (p->pressure && p->kn_mode == 1) {
+            real_t r0 = 0.0, r1 = 0.0;
+            for (int i = 0; i < NQ; ++i) {
+                r0 += f_prev[IDX(i, y0, xs[k], p->nx, p->ny)];
+                r1 += f_prev[IDX(i, y1, xs[k], p->nx, p->ny)];
+            }
+            rho_kn = (p->ny % 2) ? r0 : 0.5 * (r0 + r1);
+        }
+        node_rates(p, rho_kn, s);
         oracle_collide(fb, P_gx(p), p->gy, s, out + 9 * (size_t)k, NULL, NULL);
     }
 }

@@ -58,6 +58,8 @@ typedef struct {
     double sq_override;   /* >0: use this s_q instead of Eq. 21 (tests) */
     int same_node_bsr;    /* test-only: Eq. 20 with no x offset on the specular part */
     double r_im, a_im, gx_im; /* complex-step build: imaginary parts of r, a, gx */
+    int kn_mode;          /* pressure mode: 0 Kn from the node's own pressure; 1 from the
+                             centreline pressure p(x) of the previous step (Sec. 3.2) */
 } oracle_params;
 
 /* Lattice and matrices built from their definitions (Eq. 1, 3, 10). */

@@ -53,6 +53,7 @@ class _Params(C.Structure):
         ("sv_override", C.c_double), ("sq_override", C.c_double),
         ("same_node_bsr", C.c_int),
         ("r_im", C.c_double), ("a_im", C.c_double), ("gx_im", C.c_double),
+        ("kn_mode", C.c_int),
     ]
 
 
@@ -80,13 +81,14 @@ class OracleParams:
     r_im: float = 0.0  # imaginary parts, read by the complex-step build only
     a_im: float = 0.0
     gx_im: float = 0.0
+    kn_mode: int = 0  # pressure mode: 0 node pressure, 1 centreline pressure of the previous step
 
     def c(self) -> _Params:
         r = self.r if self.r is not None else r_from_sigma(self.sigma)
         return _Params(
             self.nx, self.ny, int(self.pressure), self.kn, self.a, r, self.b2, self.s3, self.s8,
             self.gx, self.gy, self.rho_in, self.rho_out, self.sv_override, self.sq_override,
-            int(self.same_node_bsr), self.r_im, self.a_im, self.gx_im,
+            int(self.same_node_bsr), self.r_im, self.a_im, self.gx_im, int(self.kn_mode),
         )
 
 

@@ -170,11 +170,12 @@ def test_pressure_steady_mass_balance(oracle_mod):
     assert o["q_norm"] > 1.0  # slip raises the flow above the no-slip value
 
 
-@pytest.mark.parametrize("mode", ["periodic", "pressure", "same_node"])
+@pytest.mark.parametrize("mode", ["periodic", "pressure", "same_node", "centreline_kn"])
 def test_node_local_pull_equals_push_step(oracle_mod, mode):
     r = inputs.rng(11)
-    if mode == "pressure":
-        p = oracle_mod.OracleParams(nx=9, ny=5, pressure=True, kn=0.2, rho_in=1.8)
+    if mode in ("pressure", "centreline_kn"):
+        p = oracle_mod.OracleParams(nx=9, ny=6 if mode == "centreline_kn" else 5, pressure=True, kn=0.2,
+                                    rho_in=1.8, kn_mode=int(mode == "centreline_kn"))
     else:
         p = oracle_mod.OracleParams(nx=6, ny=4, kn=0.4, gx=1e-3, gy=-4e-4,
                                     same_node_bsr=(mode == "same_node"))
@@ -220,3 +221,21 @@ def test_pressure_channel_stays_bounded_at_high_tau(oracle_mod):
     assert np.isfinite(rho).all()
     assert np.abs(uy).max() < 0.05 * np.abs(ux).max()
     assert rho.min() > 0.99 and rho.max() < 1.21
+
+
+def test_centreline_knudsen_mode_steady_state(oracle_mod):
+    """Sec. 3.2 defines the local Kn from the centreline pressure p(x).  With
+    it (one step behind, kn_mode 1) the steady channel keeps the interior mass
+    balance and differs from the per-node reading only through the small
+    transverse density variation."""
+    out = {}
+    for mode in (0, 1):
+        p = oracle_mod.OracleParams(nx=41, ny=6, pressure=True, kn=0.1, rho_in=1.5, kn_mode=mode)
+        s = oracle_mod.OracleSim(p)
+        s.step(4000, 1)
+        o = s.observables()
+        m = o["m_of_x"][1:-1]
+        assert np.abs(m - m.mean()).max() / m.mean() < 1e-6
+        out[mode] = o["mass_flow"]
+    assert out[1] == pytest.approx(out[0], rel=1e-4)
+    assert out[1] != out[0]
