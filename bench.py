@@ -32,8 +32,8 @@ if ROOT not in sys.path:
 NX, NY, KN_OUT, RATIO = 25601, 256, 0.1, 2.47
 METRIC = "D2Q9 CLB MLUPS and % HBM roofline, FP32-shifted vs FP64 at stated error"
 WORKLOAD = "pressure-driven microchannel L/H=100, Ny=256 x Nx=25601 (6.55M nodes), Kn_out=0.1, p_in/p_out=2.47"
-SWEEP_SOURCES = ["paper_1603_01955_gb300/csrc/sweep.cu", "paper_1603_01955_gb300/csrc/clb_device.cuh",
-                 "paper_1603_01955_gb300/csrc/clb_internal.h"]
+SWEEP_SOURCES = ["paper_1603_01955_gb300/csrc/sweep.cu", "paper_1603_01955_gb300/csrc/sweep_tma.cu",
+                 "paper_1603_01955_gb300/csrc/clb_device.cuh", "paper_1603_01955_gb300/csrc/clb_internal.h"]
 
 
 def sweep_source_hash() -> str:
@@ -52,10 +52,11 @@ def measured_peaks() -> tuple[float, str]:
         return 6800.0, "fallback"
 
 
-def profiled_traffic(storage: str):
-    """DRAM bytes per sweep launch from the committed ncu summary, if it was
-    taken on the current sweep source (else None)."""
-    path = os.path.join(ROOT, "profiles", f"sweep_{storage}_pressure_25601x256.md")
+def profiled_traffic(storage: str, pipeline: int):
+    """DRAM bytes per sweep launch from the committed ncu summary of that
+    engine, if it was taken on the current sweep sources (else None)."""
+    kernel = "sweep" if pipeline <= 1 else "sweep_tma"
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{storage}_pressure_25601x256.md")
     try:
         text = open(path).read()
     except OSError:
@@ -144,6 +145,24 @@ def gpu_id_for_smi(torch) -> str:
     return first if first.isdigit() else str(torch.cuda.current_device())
 
 
+def max_over_ranks(v: float, world: int, device: str) -> float:
+    """Slowest rank's time (the contract's max over ranks)."""
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_mlups(nodes: int, steps: int, t_max: float, world: int) -> float:
+    """Whole-job throughput of independent replicas: every rank updates
+    `nodes` nodes `steps` times; the job takes the slowest rank's time."""
+    return world * nodes * steps / t_max / 1e6
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -166,12 +185,6 @@ def run_gpu(args):
         if world > 1:
             dist.barrier()
 
-    def max_over_ranks(v: float) -> float:
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
 
     K, W = args.steps, args.warmup
     nodes = NX * NY
@@ -179,7 +192,8 @@ def run_gpu(args):
     results = {}
     clocks = None
     for storage in args.variants:
-        ch = clb.Channel(NX, NY, KN_OUT, drive="pressure", drive_value=RATIO, storage=storage)
+        ch = clb.Channel(NX, NY, KN_OUT, drive="pressure", drive_value=RATIO, storage=storage,
+                         pipeline=args.pipeline)
         info = ch.info()
         stream = ch.stream
         with torch.cuda.stream(stream):
@@ -200,9 +214,10 @@ def run_gpu(args):
                 barrier()
         t_total = e0.elapsed_time(e2) / 1e3
         t_sweeps = e0.elapsed_time(e1) / 1e3
-        t_total = max_over_ranks(t_total)
+        t_total = max_over_ranks(t_total, world, "cuda")
         results[storage] = dict(
-            mlups=world * nodes * K / t_total / 1e6,
+            pipeline=info["pipeline"],
+            mlups=replica_mlups(nodes, K, t_total, world),
             ms_per_step=t_total / K * 1e3,
             sweep_us=t_sweeps / K * 1e6,
             bytes_per_node=info["bytes_per_node"],
@@ -215,7 +230,7 @@ def run_gpu(args):
 
     # end to end through the C ABI with host buffers: upload the initial state
     # from pinned host memory, K sweeps, read the observables back
-    ch = clb.Channel(NX, NY, KN_OUT, drive="pressure", drive_value=RATIO, storage="fp32s")
+    ch = clb.Channel(NX, NY, KN_OUT, drive="pressure", drive_value=RATIO, storage="fp32s", pipeline=args.pipeline)
     host_f = torch.empty((9, NY, NX), dtype=torch.float64, pin_memory=True)
     host_f.numpy()[...] = ch.state()
     import numpy as np
@@ -234,7 +249,7 @@ def run_gpu(args):
         clb.clb_observables(ch.sim, -1, s, prof["ux"], prof["uy"], cols["pc"], cols["dp"], cols["m"])
         t_e2e = time.perf_counter() - t0
         barrier()
-    t_e2e = max_over_ranks(t_e2e)
+    t_e2e = max_over_ranks(t_e2e, world, "cuda")
     ch.close()
     h2d = host_f.numel() * 8
     d2h = (2 * NY + 3 * NX) * 8 + 7 * 8
@@ -244,7 +259,7 @@ def run_gpu(args):
     f32 = results["fp32s"]
     peak, peak_kind = measured_peaks()
     achieved = f32["bytes_per_node"] * nodes / (f32["sweep_us"] * 1e-6) / 1e9
-    traffic = profiled_traffic("fp32s")
+    traffic = profiled_traffic("fp32s", f32["pipeline"])
     line = {
         "metric": METRIC,
         "value": round(f32["mlups"], 1),
@@ -265,7 +280,7 @@ def run_gpu(args):
             "step": "one fused stream-collide sweep per step; one FP64 observable reduction per timed region",
             "l2": "no flush: each population buffer is 236 MB (FP32) / 472 MB (FP64), above the 129 MB L2",
             "parallelism": "replicas" if world > 1 else "single GPU",
-            "launch": {"vec": 4, "block_x": 128},
+            "launch": engine_of(f32["pipeline"]),
         },
         "roofline": {
             "bound": "hbm",
@@ -276,11 +291,11 @@ def run_gpu(args):
             "traffic": traffic,
             "peak_kind": peak_kind,
             "bytes_per_node": f32["bytes_per_node"],
-            "kernel": "sweep_kernel<float, pressure, 4>",
+            "kernel": engine_of(f32["pipeline"])["kernel"],
         },
         "variants": variants_block(results, nodes, peak),
         "e2e": {
-            "value": round(world * nodes * K / t_e2e / 1e6, 1),
+            "value": round(replica_mlups(nodes, K, t_e2e, world), 1),
             "unit": "MLUPS",
             "h2d_bytes_per_step": h2d / K,
             "d2h_bytes_per_step": d2h / K,
@@ -378,10 +393,26 @@ def errors_vs_oracle(clb, variants, ref, steps):
     return out
 
 
+# tile shapes of the TMA-staged sweep: (consumer threads, nodes per thread, stages)
+TMA_SHAPES = [(128, 4, 4), (256, 4, 3), (256, 2, 4), (256, 2, 6), (256, 1, 8), (256, 4, 4), (512, 1, 4),
+              (128, 2, 8), (512, 1, 6), (512, 1, 4), (384, 1, 4), (384, 1, 6), (512, 2, 3)]
+
+
+def engine_of(pipeline: int) -> dict:
+    if pipeline <= 1:
+        return {"pipeline": pipeline, "engine": "direct vector loads + warp shuffles", "vec": 4, "block_x": 128,
+                "kernel": "sweep_kernel<float, pressure, 4>"}
+    nc, v, st = TMA_SHAPES[pipeline - 2]
+    return {"pipeline": pipeline, "engine": "TMA bulk copies into a shared-memory ring",
+            "consumers": nc, "nodes_per_thread": v, "stages": st,
+            "kernel": f"sweep_tma_kernel<float, pressure, {nc}, {v}, {st}>"}
+
+
 def variants_block(results, nodes, peak):
     out = {}
     for storage, r in results.items():
         out[storage] = {"mlups": round(r["mlups"], 1), "sweep_us": round(r["sweep_us"], 3),
+                        "pipeline": r["pipeline"],
                         "bytes_per_node": r["bytes_per_node"],
                         "hbm_frac": round(r["bytes_per_node"] * nodes / (r["sweep_us"] * 1e-6) / 1e9 / peak, 4),
                         "mass_flow": r["mass_flow"], "clocks": r["clocks"]}
@@ -477,6 +508,8 @@ def main():
     ap.add_argument("--variants", default="fp32s,fp64,fp16s,bf16s", help="storages to time (fp32s first)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched Knudsen-sweep measurement")
     ap.add_argument("--batch-steps", type=int, default=20000)
+    ap.add_argument("--pipeline", type=int, default=0,
+                    help="sweep engine for FP32/16-bit storage (clb_opts.pipeline; 0 = library default)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -48,7 +48,7 @@ typedef enum {
     CLB_ENOMEM = 2,   /* device or host allocation failed */
     CLB_ECUDA = 3,    /* a CUDA call failed (message has the CUDA error) */
     CLB_ENUMERIC = 4, /* a NaN or Inf was seen in the fields */
-    CLB_ETIMEOUT = 5  /* reserved: a bounded device wait gave up */
+    CLB_ETIMEOUT = 5  /* a bounded device wait gave up (TMA-staged sweep); the results are invalid */
 } clb_status;
 
 typedef enum {
@@ -79,6 +79,21 @@ typedef struct {
     void* (*alloc)(size_t bytes, void* ctx);
     void (*free)(void* ptr, void* ctx);
     void* alloc_ctx;
+    /* How the sweep reads its inputs (FP32 and 16-bit storage; FP64 always 1):
+     * 0 = default, 1 = direct vector loads with warp shuffles, 2..14 = staged
+     * through shared memory by TMA bulk copies, tile shape 0..12 of the table
+     * in sweep_tma.cu (consumer threads x nodes per thread, ring stages).
+     * All give bit-identical results. */
+    int pipeline;
+    /* Local Knudsen number of a pressure channel (Sec. 3.2): 0 = from the
+     * node's own pressure (default), 1 = from the centreline pressure p(x) of
+     * the column, taken one step behind (middle row, or mean of the two middle
+     * rows).  1 uses the direct-load sweep. */
+    int kn_mode;
+    /* Testing only: >= 0 makes the TMA-staged sweep withhold the inputs of
+     * that tile in every step, so that its bounded waits expire and the next
+     * clb_sync / clb_observables returns CLB_ETIMEOUT.  -1 (default) = off. */
+    int test_withhold_tile;
 } clb_opts;
 
 void clb_opts_default(clb_opts* opts);
@@ -160,10 +175,13 @@ typedef struct {
     double kn, a, g, rho_in, rho_out;
     int64_t step;
     void* stream;         /* the cudaStream_t in use */
+    int pipeline;         /* sweep engine in use: 1 direct loads, 2.. TMA-staged tile shape (see clb_opts) */
+    int kn_mode;          /* local Knudsen number: 0 node pressure, 1 centreline pressure */
 } clb_info_t;
 clb_status clb_info(const clb_sim* sim, clb_info_t* info);
 
-/* Wait for all queued work of the simulation. */
+/* Wait for all queued work of the simulation.  CLB_ETIMEOUT if a sweep
+ * recorded an expired wait since the last check. */
 clb_status clb_sync(clb_sim* sim);
 
 /* Release everything the simulation owns; NULL is accepted. */

@@ -35,6 +35,7 @@ class clb_opts(C.Structure):
         ("b2", C.c_double), ("sigma", C.c_double), ("s3", C.c_double), ("s8", C.c_double),
         ("rho_out", C.c_double), ("storage", C.c_int), ("vec", C.c_int), ("block_x", C.c_int),
         ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
+        ("pipeline", C.c_int), ("kn_mode", C.c_int), ("test_withhold_tile", C.c_int),
     ]
 
 
@@ -53,6 +54,7 @@ class clb_info_t(C.Structure):
         ("bytes_per_node", C.c_double), ("sv", C.c_double), ("sq", C.c_double), ("r", C.c_double),
         ("kn", C.c_double), ("a", C.c_double), ("g", C.c_double), ("rho_in", C.c_double),
         ("rho_out", C.c_double), ("step", C.c_int64), ("stream", C.c_void_p),
+        ("pipeline", C.c_int), ("kn_mode", C.c_int),
     ]
 
 
@@ -201,7 +203,7 @@ class Channel:
 
     def __init__(self, nx, ny, kn, a=2.0, r=-1.0, drive="body_force", drive_value=0.0, storage="fp32s",
                  vec=0, block_x=0, b2=0.55, sigma=1.0, s3=1.1, s8=1.2, rho_out=1.0, stream=None,
-                 torch_allocator=True):
+                 torch_allocator=True, pipeline=0, kn_mode=0, test_withhold_tile=-1, alloc_hook=None):
         import torch
 
         self.nx, self.ny = int(nx), int(ny)
@@ -215,11 +217,16 @@ class Channel:
         o.b2, o.sigma, o.s3, o.s8, o.rho_out = b2, sigma, s3, s8, rho_out
         o.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
         o.vec, o.block_x = int(vec), int(block_x)
+        o.pipeline = int(pipeline)
+        o.kn_mode = int(kn_mode)
+        o.test_withhold_tile = int(test_withhold_tile)
         o.stream = C.c_void_p(self._stream.cuda_stream)
         if torch_allocator:
             s = self._stream
 
             def _alloc(n, ctx):
+                if alloc_hook is not None and not alloc_hook(int(n)):
+                    return None  # the caller's hook refuses this allocation
                 try:
                     return torch.cuda.caching_allocator_alloc(int(n), dev, s)
                 except Exception:  # noqa: BLE001 - reported to the library as NULL

@@ -111,8 +111,10 @@ __device__ __forceinline__ void macro_dev(const R d[9], R& drho, R& jx, R& jy) {
 // deviations d relative to R = ref.  MODE_PERIODIC: body force F, constant
 // rates.  MODE_PRESSURE: no force, s_v and s_q from the local Knudsen number
 // Kn = Kn_out rho_out / rho (Sec. 3.2) through Eq. 18 and Eq. 21.
+// rho_kn (pressure channel, optional): the density that sets the local
+// Knudsen number when it is not the node's own (the column's centreline).
 template <typename R, int MODE>
-__device__ __forceinline__ void collide(R (&d)[9], R ref, const KC<R>& c) {
+__device__ __forceinline__ void collide(R (&d)[9], R ref, const KC<R>& c, const R* rho_kn = nullptr) {
     // raw moments of Eq. 8 (deviation parts)
     const R a57 = d[5] + d[7], a68 = d[6] + d[8];
     const R p57 = d[5] - d[7], p86 = d[8] - d[6];
@@ -139,7 +141,7 @@ __device__ __forceinline__ void collide(R (&d)[9], R ref, const KC<R>& c) {
     if (MODE == MODE_PRESSURE) {
         // tau = A/q, q = rho + B; 1/s_v = 1/2 + tau (Eq. 18);
         // 1/s_q = 1/2 + 3/(16 tau) + (pi B2/4) tau (Eq. 21)
-        const R q = rho + c.B;
+        const R q = (rho_kn ? *rho_kn : rho) + c.B;
         sv4 = R(0.25) * q * rcp(R(0.5) * q + c.A);
         sq4 = R(0.25) * q * rcp(q * (R(0.5) + c.A316 * q) + c.CA);
     } else {
@@ -204,6 +206,73 @@ __device__ __forceinline__ void collide(R (&d)[9], R ref, const KC<R>& c) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) d[i] += S[i];
     }
+}
+
+// ------------------------------------------------- pressure boundary columns
+
+// Pre-collision deviations at one interior node (x in 1..nx-2) of a pressure
+// channel, gathered element by element; used only to rebuild the end columns.
+template <class T, class R>
+__device__ void gather_node(const SweepArgs& a, const KC<R>& c, const T* fin, int x, int y, R o[9]) {
+    const long long P = a.plane;
+    const T* row = fin + (long long)y * a.pitch + a.xoff;
+    auto at = [&](int i, int dy, int xx) -> R {
+        return Codec<T>::dec(__ldg(row + i * P + (long long)dy * a.pitch + xx), c.isc);
+    };
+    const int rt = a.row_type[y];
+    const R sha = c.sha, shd = c.shd;  // source at x-1; the source at x+1 gets the negative
+    o[0] = at(0, 0, x);
+    o[1] = at(1, 0, x - 1) + sha;
+    o[3] = at(3, 0, x + 1) - sha;
+    if (rt & ROW_BOTTOM) {
+        o[2] = at(4, 0, x);
+        o[5] = c.r * at(7, 0, x) + c.rc * (at(8, 0, x - 1) + shd);
+        o[6] = c.r * at(8, 0, x) + c.rc * (at(7, 0, x + 1) - shd);
+    } else {
+        o[2] = at(2, -1, x);
+        o[5] = at(5, -1, x - 1) + shd;
+        o[6] = at(6, -1, x + 1) - shd;
+    }
+    if (rt & ROW_TOP) {
+        o[4] = at(2, 0, x);
+        o[7] = c.r * at(5, 0, x) + c.rc * (at(6, 0, x + 1) - shd);
+        o[8] = c.r * at(6, 0, x) + c.rc * (at(5, 0, x - 1) + shd);
+    } else {
+        o[4] = at(4, 1, x);
+        o[7] = at(7, 1, x + 1) - shd;
+        o[8] = at(8, 1, x - 1) + shd;
+    }
+}
+
+// Pressure column rebuilt by linear extrapolation (reading of Sec. 3.2):
+//   f_i(b) = f^eq_i(rho_b, u_b) + f^neq_i(b+d),  u_b = 2 u(b+d) - u(b+2d),
+//   f^neq = f - f^eq(rho, u),
+// with d = +1 at the inlet (rho_b = rho_in) and -1 at the outlet (rho_out):
+// the velocity is extrapolated linearly, the non-equilibrium part comes from
+// the first interior neighbour (a linear extrapolation of it as well would
+// amplify the shortest x-wavelength threefold and diverge at tau ~ 30).
+// Output: deviations relative to R(b).
+template <class T, class R>
+__device__ __forceinline__ void rebuild_column(const SweepArgs& a, const KC<R>& c, const T* fin, int x, int y,
+                                            bool inlet, R* out) {
+    const int dir = inlet ? 1 : -1;
+    R n1[9], n2[9], e1[9], eb[9];
+    gather_node<T, R>(a, c, fin, x + dir, y, n1);
+    gather_node<T, R>(a, c, fin, x + 2 * dir, y, n2);
+    R dr1, jx1, jy1, dr2, jx2, jy2;
+    macro_dev(n1, dr1, jx1, jy1);
+    macro_dev(n2, dr2, jx2, jy2);
+    const R r1 = c.ref0 + c.slope * R(x + dir) + dr1;
+    const R r2 = c.ref0 + c.slope * R(x + 2 * dir) + dr2;
+    const R u1x = jx1 / r1, u1y = jy1 / r1, u2x = jx2 / r2, u2y = jy2 / r2;
+    feq_dev(dr1, r1, u1x, u1y, e1);
+    const R drb = inlet ? c.drho_in : c.drho_out;
+    const R rb = c.ref0 + c.slope * R(x) + drb;
+    feq_dev(drb, rb, R(2) * u1x - u2x, R(2) * u1y - u2y, eb);
+    // the neighbour's deviations are relative to R(x+d); f^neq does not depend
+    // on the reference, so only the equilibrium carries R(b)
+#pragma unroll
+    for (int i = 0; i < 9; ++i) out[i] = eb[i] + (n1[i] - e1[i]);
 }
 
 }  // namespace clb

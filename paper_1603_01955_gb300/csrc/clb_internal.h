@@ -54,6 +54,17 @@ struct SweepArgs {
     double ref0, ref_slope;
     double drho_in, drho_out; // rho_in - R(0), rho_out - R(nx-1)
     double store_scale;       // stored value = deviation * store_scale (16-bit formats)
+    // Centreline Knudsen number (pressure channel, Sec. 3.2): kn_mode 1 takes
+    // the rates of column x from the centreline density of the last step,
+    // rc_in[x] (rows yc0 and yc1, averaged), and the centre rows write this
+    // step's densities to rc_out.  rc arrays hold 2 x rc_stride elements of
+    // the compute type (one block per centre row).
+    int kn_mode;
+    int yc0, yc1;
+    int rc_stride;
+    const void* rc_in;
+    void* rc_out;
+    int withhold_tile;        // testing: TMA tile whose inputs are never sent (-1: none)
     KC<float> kf;             // the constants above, derived, in FP32
     KC<double> kd;            // ... and in FP64
 };
@@ -77,5 +88,11 @@ cudaError_t launch_sweep(int storage, int mode, int vec, int block_x, const Swee
 
 // True if (storage, vec) has a compiled sweep.
 bool sweep_supported(int storage, int vec);
+
+// The sweep with TMA-staged inputs (FP32 and 16-bit storage); variant picks
+// the tile shape.  *status collects error bits of bounded waits that expired.
+cudaError_t launch_sweep_tma(int storage, int mode, int variant, const SweepArgs& a, cudaStream_t stream,
+                             unsigned* status);
+int tma_variant_count();
 
 }  // namespace clb

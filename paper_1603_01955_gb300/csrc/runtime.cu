@@ -80,6 +80,13 @@ struct clb_sim {
     uint8_t* col_type = nullptr;
     size_t col_bytes = 0;
     double* obs = nullptr;  // device scratch of the observable reductions
+    unsigned* status = nullptr;  // error bits of bounded device waits
+    int pipeline = 1;       // 1 direct loads, 2.. TMA-staged variants
+    int withhold_tile = -1; // testing: TMA tile whose inputs are withheld
+    int kn_mode = 0;        // 1: centreline Knudsen number (pressure channel)
+    void* rc = nullptr;     // centreline densities: [2 sides][2 rows][rc_stride], compute type
+    int rc_stride = 0;
+    int yc0 = 0, yc1 = 0;   // centre rows
     ObsLayout L{};
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -170,6 +177,21 @@ __global__ void from_canonical_kernel(const double* in, T* f, int nx, int ny, in
         if (periodic) {
             if (x == 0 && c_ex[i] < 0) row[nx] = v;
             if (x == nx - 1 && c_ex[i] > 0) row[-1] = v;
+        }
+    }
+}
+
+// Centre-row densities of a state into rc[2][stride] (compute type RC).
+template <class T, class RC>
+__global__ void centre_density_kernel(const T* f, RC* rc, int nx, int pitch, int xoff, long long plane, int yc0,
+                                      int yc1, int stride, double ref0, double ref_slope, double isc) {
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < nx; x += gridDim.x * blockDim.x) {
+        for (int slot = 0; slot < 2; ++slot) {
+            const int y = slot ? yc1 : yc0;
+            const T* row = f + (long long)y * pitch + xoff + x;
+            double rho = ref0 + ref_slope * x;
+            for (int i = 0; i < 9; ++i) rho += (double)Codec<T>::dec(row[i * plane], RT<T>(isc));
+            rc[slot * stride + x] = RC(rho);
         }
     }
 }
@@ -315,10 +337,30 @@ SweepArgs make_args(const clb_sim* s) {
     a.drho_in = s->rho_in - s->ref_at(0);
     a.drho_out = s->rho_out - s->ref_at(s->nx - 1);
     a.store_scale = s->store_scale;
+    a.kn_mode = s->kn_mode;
+    a.withhold_tile = s->withhold_tile;
+    a.yc0 = s->yc0;
+    a.yc1 = s->yc1;
+    a.rc_stride = s->rc_stride;
     derive_constants(a);
     return a;
 }
 
+
+// Centre-row densities of the current state into the rc side read by the
+// next sweep (centreline Knudsen number only).
+cudaError_t refresh_centre(clb_sim* s) {
+    if (s->kn_mode != 1 || s->drive != CLB_DRIVE_PRESSURE) return cudaSuccess;
+    return with_storage(s->storage, [&](auto tag) {
+        using T = decltype(tag);
+        using RC = RT<T>;
+        RC* side = static_cast<RC*>(s->rc) + (size_t)s->cur * 2 * s->rc_stride;
+        centre_density_kernel<T, RC><<<grid_for(s->nx, 256), 256, 0, s->stream>>>(
+            static_cast<const T*>(s->buf[s->cur]), side, s->nx, s->pitch, s->xoff, s->plane, s->yc0, s->yc1,
+            s->rc_stride, s->ref0, s->ref_slope, 1.0 / s->store_scale);
+        return cudaGetLastError();
+    });
+}
 
 cudaError_t launch_init(clb_sim* s, void* buf, double rho_a, double rho_slope) {
     const long long n = 9LL * s->nx * s->ny;
@@ -364,6 +406,7 @@ extern "C" {
 void clb_opts_default(clb_opts* o) {
     if (!o) return;
     std::memset(o, 0, sizeof *o);
+    o->test_withhold_tile = -1;
     o->b2 = 0.55;
     o->sigma = 1.0;
     o->s3 = 1.1;
@@ -382,6 +425,8 @@ clb_status clb_destroy(clb_sim* s) {
     s->dfree(s->row_type);
     s->dfree(s->col_type);
     s->dfree(s->obs);
+    s->dfree(s->status);
+    s->dfree(s->rc);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
     delete s;
     return CLB_OK;
@@ -416,6 +461,9 @@ clb_status clb_create(int nx, int ny, double kn, double a, double r, clb_drive d
     int vec = o.vec ? o.vec : (o.storage == CLB_FP64 ? 2 : 4);
     if (!sweep_supported(o.storage, vec)) return fail(CLB_EINVAL, "clb_create: vec = %d not available", vec);
     int block_x = o.block_x ? o.block_x : 128;
+    if (o.pipeline < 0 || o.pipeline > 1 + tma_variant_count())
+        return fail(CLB_EINVAL, "clb_create: pipeline = %d must be 0..%d", o.pipeline, 1 + tma_variant_count());
+    if (o.kn_mode < 0 || o.kn_mode > 1) return fail(CLB_EINVAL, "clb_create: kn_mode = %d must be 0 or 1", o.kn_mode);
     if (block_x < 32 || block_x > 256 || block_x % 32)
         return fail(CLB_EINVAL, "clb_create: block_x = %d must be a multiple of 32 in 32..256", block_x);
 
@@ -426,6 +474,11 @@ clb_status clb_create(int nx, int ny, double kn, double a, double r, clb_drive d
     s->storage = o.storage;
     s->vec = vec;
     s->block_x = block_x;
+    s->kn_mode = (drive == CLB_DRIVE_PRESSURE) ? o.kn_mode : 0;
+    s->withhold_tile = o.test_withhold_tile;
+    s->pipeline = (o.storage == CLB_FP64 || s->kn_mode == 1) ? 1 : (o.pipeline == 0 ? 1 : o.pipeline);
+    s->yc0 = (ny % 2) ? (ny - 1) / 2 : ny / 2 - 1;
+    s->yc1 = (ny % 2) ? s->yc0 : ny / 2;
     s->drive = drive;
     s->kn = kn;
     s->a = a;
@@ -486,7 +539,10 @@ clb_status clb_create(int nx, int ny, double kn, double a, double r, clb_drive d
     s->row_type = static_cast<uint8_t*>(s->dalloc(ny));
     s->col_type = static_cast<uint8_t*>(s->dalloc(s->col_bytes));
     s->obs = static_cast<double*>(s->dalloc(s->L.total * sizeof(double)));
-    if (!s->buf[0] || !s->buf[1] || !s->row_type || !s->col_type || !s->obs) {
+    s->status = static_cast<unsigned*>(s->dalloc(sizeof(unsigned)));
+    s->rc_stride = ((nx + 16 + 31) / 32) * 32;
+    s->rc = s->dalloc((size_t)4 * s->rc_stride * (o.storage == CLB_FP64 ? 8 : 4));
+    if (!s->buf[0] || !s->buf[1] || !s->row_type || !s->col_type || !s->obs || !s->status || !s->rc) {
         clb_destroy(s);
         return fail(CLB_ENOMEM, "clb_create: device allocation of %zu bytes failed", 2 * s->buf_bytes);
     }
@@ -511,8 +567,11 @@ clb_status clb_create(int nx, int ny, double kn, double a, double r, clb_drive d
     chk(cudaMemsetAsync(s->buf[0], 0, s->buf_bytes, s->stream), "memset");
     chk(cudaMemsetAsync(s->buf[1], 0, s->buf_bytes, s->stream), "memset");
     chk(cudaMemsetAsync(s->obs, 0, s->L.total * sizeof(double), s->stream), "memset");
+    chk(cudaMemsetAsync(s->status, 0, sizeof(unsigned), s->stream), "memset");
     const double rho_slope = (drive == CLB_DRIVE_PRESSURE) ? (s->rho_out - s->rho_in) / (double)(nx - 1) : 0.0;
+    chk(cudaMemsetAsync(s->rc, 0, (size_t)4 * s->rc_stride * (o.storage == CLB_FP64 ? 8 : 4), s->stream), "memset");
     chk(launch_init(s, s->buf[0], s->rho_in, rho_slope), "init");
+    chk(refresh_centre(s), "centre densities");
     chk(cudaStreamSynchronize(s->stream), "sync");
     if (st != CLB_OK) {
         clb_destroy(s);
@@ -527,10 +586,15 @@ clb_status clb_step(clb_sim* s, int64_t n) {
     if (n < 0) return fail(CLB_EINVAL, "clb_step: n < 0");
     const int mode = s->drive == CLB_DRIVE_PRESSURE ? MODE_PRESSURE : MODE_PERIODIC;
     SweepArgs a = make_args(s);
+    const size_t rc_side = (size_t)2 * s->rc_stride * (s->storage == CLB_FP64 ? 8 : 4);
     for (int64_t t = 0; t < n; ++t) {
         a.fin = s->buf[s->cur];
         a.fout = s->buf[s->cur ^ 1];
-        cudaError_t e = launch_sweep(s->storage, mode, s->vec, s->block_x, a, s->stream);
+        a.rc_in = static_cast<const char*>(s->rc) + s->cur * rc_side;
+        a.rc_out = static_cast<char*>(s->rc) + (s->cur ^ 1) * rc_side;
+        cudaError_t e = s->pipeline >= 2
+                            ? launch_sweep_tma(s->storage, mode, s->pipeline - 2, a, s->stream, s->status)
+                            : launch_sweep(s->storage, mode, s->vec, s->block_x, a, s->stream);
         if (e != cudaSuccess) return fail(CLB_ECUDA, "clb_step: sweep launch: %s", cudaGetErrorString(e));
         s->cur ^= 1;
         ++s->step;
@@ -538,10 +602,22 @@ clb_status clb_step(clb_sim* s, int64_t n) {
     return CLB_OK;
 }
 
+// Read and clear the device status word; CLB_ETIMEOUT if a wait expired.
+static clb_status check_status(clb_sim* s, const char* who) {
+    unsigned st = 0;
+    CUDA_OR(cudaMemcpyAsync(&st, s->status, sizeof st, cudaMemcpyDeviceToHost, s->stream));
+    CUDA_OR(cudaStreamSynchronize(s->stream));
+    if (st) {
+        CUDA_OR(cudaMemsetAsync(s->status, 0, sizeof(unsigned), s->stream));
+        return fail(CLB_ETIMEOUT, "%s: a sweep gave up waiting for its staged inputs (bits %u)", who, st);
+    }
+    return CLB_OK;
+}
+
 clb_status clb_sync(clb_sim* s) {
     if (!s) return fail(CLB_EINVAL, "clb_sync: sim is NULL");
     CUDA_OR(cudaStreamSynchronize(s->stream));
-    return CLB_OK;
+    return check_status(s, "clb_sync");
 }
 
 clb_status clb_info(const clb_sim* s, clb_info_t* info) {
@@ -564,6 +640,8 @@ clb_status clb_info(const clb_sim* s, clb_info_t* info) {
     info->rho_out = s->rho_out;
     info->step = s->step;
     info->stream = s->stream;
+    info->pipeline = s->pipeline;
+    info->kn_mode = s->kn_mode;
     return CLB_OK;
 }
 
@@ -604,6 +682,7 @@ clb_status clb_set_state(clb_sim* s, const double* host_f) {
             return cudaGetLastError();
         });
     }
+    if (e == cudaSuccess) e = refresh_centre(s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) st = fail(CLB_ECUDA, "clb_set_state: %s", cudaGetErrorString(e));
     s->dfree(tmp);
@@ -675,6 +754,8 @@ clb_status clb_observables(clb_sim* s, int profile_col, clb_scalars* sc, double*
         s->prev_mass_flow = mbar;
         s->have_prev = true;
     }
+    clb_status st = check_status(s, "clb_observables");
+    if (st != CLB_OK) return st;
     if (nbad > 0) return fail(CLB_ENUMERIC, "clb_observables: %.0f nodes with a non-finite density or velocity", nbad);
     return CLB_OK;
 }

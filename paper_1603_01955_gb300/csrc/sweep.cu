@@ -140,71 +140,6 @@ __device__ __forceinline__ void add_shift(R (&o)[V], R s) {
     for (int k = 0; k < V; ++k) o[k] += s;
 }
 
-// Pre-collision deviations at one interior node (x in 1..nx-2) of a pressure
-// channel, gathered element by element; used only to rebuild the end columns.
-template <class T, class R>
-__device__ void gather_node(const SweepArgs& a, const KC<R>& c, const T* fin, int x, int y, R o[9]) {
-    const long long P = a.plane;
-    const T* row = fin + (long long)y * a.pitch + a.xoff;
-    auto at = [&](int i, int dy, int xx) -> R {
-        return Codec<T>::dec(__ldg(row + i * P + (long long)dy * a.pitch + xx), c.isc);
-    };
-    const int rt = a.row_type[y];
-    const R sha = c.sha, shd = c.shd;  // source at x-1; the source at x+1 gets the negative
-    o[0] = at(0, 0, x);
-    o[1] = at(1, 0, x - 1) + sha;
-    o[3] = at(3, 0, x + 1) - sha;
-    if (rt & ROW_BOTTOM) {
-        o[2] = at(4, 0, x);
-        o[5] = c.r * at(7, 0, x) + c.rc * (at(8, 0, x - 1) + shd);
-        o[6] = c.r * at(8, 0, x) + c.rc * (at(7, 0, x + 1) - shd);
-    } else {
-        o[2] = at(2, -1, x);
-        o[5] = at(5, -1, x - 1) + shd;
-        o[6] = at(6, -1, x + 1) - shd;
-    }
-    if (rt & ROW_TOP) {
-        o[4] = at(2, 0, x);
-        o[7] = c.r * at(5, 0, x) + c.rc * (at(6, 0, x + 1) - shd);
-        o[8] = c.r * at(6, 0, x) + c.rc * (at(5, 0, x - 1) + shd);
-    } else {
-        o[4] = at(4, 1, x);
-        o[7] = at(7, 1, x + 1) - shd;
-        o[8] = at(8, 1, x - 1) + shd;
-    }
-}
-
-// Pressure column rebuilt by linear extrapolation (reading of Sec. 3.2):
-//   f_i(b) = f^eq_i(rho_b, u_b) + f^neq_i(b+d),  u_b = 2 u(b+d) - u(b+2d),
-//   f^neq = f - f^eq(rho, u),
-// with d = +1 at the inlet (rho_b = rho_in) and -1 at the outlet (rho_out):
-// the velocity is extrapolated linearly, the non-equilibrium part comes from
-// the first interior neighbour (a linear extrapolation of it as well would
-// amplify the shortest x-wavelength threefold and diverge at tau ~ 30).
-// Output: deviations relative to R(b).
-template <class T, class R>
-__device__ __forceinline__ void rebuild_column(const SweepArgs& a, const KC<R>& c, const T* fin, int x, int y,
-                                            bool inlet, R* out) {
-    const int dir = inlet ? 1 : -1;
-    R n1[9], n2[9], e1[9], eb[9];
-    gather_node<T, R>(a, c, fin, x + dir, y, n1);
-    gather_node<T, R>(a, c, fin, x + 2 * dir, y, n2);
-    R dr1, jx1, jy1, dr2, jx2, jy2;
-    macro_dev(n1, dr1, jx1, jy1);
-    macro_dev(n2, dr2, jx2, jy2);
-    const R r1 = c.ref0 + c.slope * R(x + dir) + dr1;
-    const R r2 = c.ref0 + c.slope * R(x + 2 * dir) + dr2;
-    const R u1x = jx1 / r1, u1y = jy1 / r1, u2x = jx2 / r2, u2y = jy2 / r2;
-    feq_dev(dr1, r1, u1x, u1y, e1);
-    const R drb = inlet ? c.drho_in : c.drho_out;
-    const R rb = c.ref0 + c.slope * R(x) + drb;
-    feq_dev(drb, rb, R(2) * u1x - u2x, R(2) * u1y - u2y, eb);
-    // the neighbour's deviations are relative to R(x+d); f^neq does not depend
-    // on the reference, so only the equilibrium carries R(b)
-#pragma unroll
-    for (int i = 0; i < 9; ++i) out[i] = eb[i] + (n1[i] - e1[i]);
-}
-
 template <class T, int MODE, int V>
 __global__ void __launch_bounds__(256, MinBlocks<T>::value) sweep_kernel(const SweepArgs a) {
     using R = typename Codec<T>::R;
@@ -336,13 +271,30 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) sweep_kernel(const S
         }
     }
 
+    // centreline Knudsen number: the column's centre density of the last step
+    R rk[V];
+    const bool centre_kn = MODE == MODE_PRESSURE && a.kn_mode == 1;
+    if (centre_kn) {
+        const R* rc0 = static_cast<const R*>(a.rc_in);
+        const R* rc1 = rc0 + a.rc_stride;
+#pragma unroll
+        for (int k = 0; k < V; ++k)
+            rk[k] = a.yc0 == a.yc1 ? rc0[x0 + k] : R(0.5) * (rc0[x0 + k] + rc1[x0 + k]);
+    }
 #pragma unroll
     for (int k = 0; k < V; ++k) {
         R d[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) d[i] = f[i][k];
         const R ref = (MODE == MODE_PRESSURE) ? c.ref0 + c.slope * R(x0 + k) : c.ref0;
-        collide<R, MODE>(d, ref, c);
+        if (centre_kn && (y == a.yc0 || y == a.yc1) && x0 + k < a.nx) {
+            R dr = d[0];
+#pragma unroll
+            for (int i = 1; i < 9; ++i) dr += d[i];
+            R* out = static_cast<R*>(a.rc_out) + (y == a.yc0 ? 0 : a.rc_stride);
+            out[x0 + k] = ref + dr;
+        }
+        collide<R, MODE>(d, ref, c, centre_kn ? &rk[k] : nullptr);
 #pragma unroll
         for (int i = 0; i < 9; ++i) f[i][k] = d[i];
     }

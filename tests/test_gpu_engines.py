@@ -1,0 +1,57 @@
+"""The TMA-staged sweep (pipeline 2-4) against the direct-load sweep
+(pipeline 1): node for node the same arithmetic, so the states must agree
+bit for bit, on random perturbed states, ragged sizes (tiles of 512 or 1024
+columns, rows of one node), both drives and every non-FP64 storage.  The
+direct sweep itself is checked against the oracle in test_gpu_parity.py."""
+import numpy as np
+import pytest
+
+import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def clb():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1603_01955_gb300.clb as clb
+
+    return clb
+
+
+SHAPES = [(5, 3, "body_force"), (513, 1, "body_force"), (1030, 7, "body_force"), (4, 2, "pressure"),
+          (600, 4, "pressure"), (1601, 16, "pressure")]
+
+
+@pytest.mark.parametrize("storage", ["fp32s", "fp16s", "bf16s"])
+@pytest.mark.parametrize("nx,ny,drive", SHAPES)
+def test_tma_pipelines_bitwise_equal_direct(clb, oracle_mod, storage, nx, ny, drive):
+    value = 1.8 if drive == "pressure" else 2e-4
+    ref = clb.Channel(nx, ny, 0.2, drive=drive, drive_value=value, storage=storage, pipeline=1)
+    f0 = inputs.perturb(inputs.rng(nx * 7 + ny), ref.state(), 0.05)
+    ref.set_state(f0)
+    ref.step(57)
+    want = ref.state()
+    for pipeline in range(2, 15):
+        ch = clb.Channel(nx, ny, 0.2, drive=drive, drive_value=value, storage=storage, pipeline=pipeline)
+        ch.set_state(f0)
+        ch.step(57)
+        np.testing.assert_array_equal(ch.state(), want, err_msg=f"pipeline {pipeline}")
+        ch.sync()
+        ch.close()
+
+
+def test_tma_full_size_bitwise_equal_direct(clb):
+    c = inputs.PRESSURE_25601x256
+    states = []
+    for pipeline in (1, 2):
+        ch = clb.Channel(c["nx"], c["ny"], c["kn_out"], drive="pressure", drive_value=c["ratio"], storage="fp32s",
+                         pipeline=pipeline)
+        ch.step(25)
+        ch.sync()
+        states.append(ch.state())
+        ch.close()
+    np.testing.assert_array_equal(states[0], states[1])

@@ -292,3 +292,35 @@ def test_16bit_edge_sizes(clb, oracle_mod, storage, nx, ny, drive, vec):
     so = orc.state()
     # the initial state itself is rounded to 16 bits: one more rounding step
     assert np.abs(ch.state() - so).max() <= tol16(storage, 101) * dev_scale(so, oracle_mod, drive, value)
+
+
+# ------------------------------------------- centreline Knudsen number (Sec. 3.2)
+
+def centre_pair(clb, oracle_mod, nx, ny, kn, value, storage):
+    ch = clb.Channel(nx, ny, kn, drive="pressure", drive_value=value, storage=storage, kn_mode=1)
+    orc = oracle_mod.OracleSim(oracle_mod.OracleParams(nx=nx, ny=ny, pressure=True, kn=kn, rho_in=value,
+                                                       kn_mode=1))
+    return ch, orc
+
+
+@pytest.mark.parametrize("kn_out", [0.0194, 0.2])
+def test_fp64_centreline_kn_1601x16_1000_steps(clb, oracle_mod, kn_out):
+    ch, orc = centre_pair(clb, oracle_mod, 1601, 16, kn_out, 2.0, "fp64")
+    ch.step(1000)
+    orc.step(1000)
+    assert per_pop_rel(ch.state(), orc.state()) <= TOL64
+
+
+@pytest.mark.parametrize("nx,ny,storage", [(37, 5, "fp64"), (130, 6, "fp64"), (37, 5, "fp32s"), (130, 6, "fp32s")])
+def test_centreline_kn_random_states(clb, oracle_mod, nx, ny, storage):
+    ch, orc = centre_pair(clb, oracle_mod, nx, ny, 0.15, 1.6, storage)
+    f0 = inputs.perturb(inputs.rng(nx + ny), orc.state(), 0.1)
+    ch.set_state(f0)
+    orc.set_state(f0)
+    ch.step(300)
+    orc.step(300)
+    so = orc.state()
+    if storage == "fp64":
+        assert per_pop_rel(ch.state(), so) <= TOL64
+    else:
+        assert np.abs(ch.state() - so).max() <= tol32(300) * dev_scale(so, oracle_mod, "pressure", 1.6)
