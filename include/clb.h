@@ -79,11 +79,13 @@ typedef struct {
     void* (*alloc)(size_t bytes, void* ctx);
     void (*free)(void* ptr, void* ctx);
     void* alloc_ctx;
-    /* How the sweep reads its inputs (FP32 and 16-bit storage; FP64 always 1):
-     * 0 = default, 1 = direct vector loads with warp shuffles, 2..14 = staged
-     * through shared memory by TMA bulk copies, tile shape 0..12 of the table
-     * in sweep_tma.cu (consumer threads x nodes per thread, ring stages).
-     * All give bit-identical results. */
+    /* How the sweep reads its inputs (FP32 and 16-bit storage; FP64 and
+     * kn_mode 1 always 1): 0 = default (14 for FP32_SHIFTED, 3 for the 16-bit
+     * storages), 1 = direct vector loads with warp shuffles (the only engine
+     * that vec and block_x configure), 2..14 = staged through shared memory by
+     * TMA bulk copies, tile shape 0..12 of the table in sweep_tma.cu (consumer
+     * threads x nodes per thread, ring stages).  All give bit-identical
+     * results. */
     int pipeline;
     /* Local Knudsen number of a pressure channel (Sec. 3.2): 0 = from the
      * node's own pressure (default), 1 = from the centreline pressure p(x) of

@@ -476,7 +476,16 @@ clb_status clb_create(int nx, int ny, double kn, double a, double r, clb_drive d
     s->block_x = block_x;
     s->kn_mode = (drive == CLB_DRIVE_PRESSURE) ? o.kn_mode : 0;
     s->withhold_tile = o.test_withhold_tile;
-    s->pipeline = (o.storage == CLB_FP64 || s->kn_mode == 1) ? 1 : (o.pipeline == 0 ? 1 : o.pipeline);
+    // Default engine: the TMA tile shape that was fastest on the 25601 x 256
+    // pressure channel for the storage (512 x 2 nodes, 3 stages for FP32;
+    // 256 x 4 nodes, 3 stages for 16-bit); FP64 and the centreline Knudsen
+    // mode always take the direct-load sweep.
+    if (o.storage == CLB_FP64 || s->kn_mode == 1)
+        s->pipeline = 1;
+    else if (o.pipeline != 0)
+        s->pipeline = o.pipeline;
+    else
+        s->pipeline = (o.storage == CLB_FP32_SHIFTED) ? 14 : 3;
     s->yc0 = (ny % 2) ? (ny - 1) / 2 : ny / 2 - 1;
     s->yc1 = (ny % 2) ? s->yc0 : ny / 2;
     s->drive = drive;

@@ -1,4 +1,4 @@
-"""The TMA-staged sweep (pipeline 2-4) against the direct-load sweep
+"""The TMA-staged sweep (pipeline 2-14) against the direct-load sweep
 (pipeline 1): node for node the same arithmetic, so the states must agree
 bit for bit, on random perturbed states, ragged sizes (tiles of 512 or 1024
 columns, rows of one node), both drives and every non-FP64 storage.  The
@@ -47,7 +47,7 @@ def test_tma_pipelines_bitwise_equal_direct(clb, oracle_mod, storage, nx, ny, dr
 def test_tma_full_size_bitwise_equal_direct(clb):
     c = inputs.PRESSURE_25601x256
     states = []
-    for pipeline in (1, 2):
+    for pipeline in (1, 2, 0):
         ch = clb.Channel(c["nx"], c["ny"], c["kn_out"], drive="pressure", drive_value=c["ratio"], storage="fp32s",
                          pipeline=pipeline)
         ch.step(25)
@@ -55,3 +55,12 @@ def test_tma_full_size_bitwise_equal_direct(clb):
         states.append(ch.state())
         ch.close()
     np.testing.assert_array_equal(states[0], states[1])
+    np.testing.assert_array_equal(states[0], states[2])
+
+
+@pytest.mark.parametrize("storage,kn_mode,want", [("fp64", 0, 1), ("fp32s", 0, 14), ("fp16s", 0, 3),
+                                                  ("bf16s", 0, 3), ("fp32s", 1, 1)])
+def test_default_engine(clb, storage, kn_mode, want):
+    ch = clb.Channel(40, 4, 0.2, drive="pressure", drive_value=1.5, storage=storage, kn_mode=kn_mode)
+    assert ch.info()["pipeline"] == want
+    ch.close()

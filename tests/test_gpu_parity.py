@@ -217,8 +217,10 @@ def test_fp32_pressure_channel_1601x16_1000_steps(clb, oracle_mod, kn_out):
 @pytest.mark.parametrize("nx,ny,drive,vec,block_x", EDGE)
 def test_fp32_edge_sizes_and_launch_shapes(clb, oracle_mod, nx, ny, drive, vec, block_x):
     value = 1.7 if drive == "pressure" else 3e-4
-    for v in sorted({vec, 4}):
-        ch, orc = pair(clb, oracle_mod, nx, ny, 0.3, drive, value, storage="fp32s", vec=v, block_x=block_x)
+    # the direct-load sweep at the given launch shapes, then the default engine
+    launches = [dict(vec=v, block_x=block_x, pipeline=1) for v in sorted({vec, 4})] + [{}]
+    for launch in launches:
+        ch, orc = pair(clb, oracle_mod, nx, ny, 0.3, drive, value, storage="fp32s", **launch)
         r = inputs.rng(nx * 100 + ny)
         f0 = inputs.perturb(r, orc.state(), 0.1)
         ch.set_state(f0)
@@ -283,15 +285,16 @@ def test_16bit_pressure_channel_1601x16_1000_steps(clb, oracle_mod, storage, kn_
                                              (4, 2, "pressure", 4), (131, 5, "pressure", 8)])
 def test_16bit_edge_sizes(clb, oracle_mod, storage, nx, ny, drive, vec):
     value = 1.7 if drive == "pressure" else 3e-4
-    ch, orc = pair(clb, oracle_mod, nx, ny, 0.3, drive, value, storage=storage, vec=vec, block_x=32)
-    f0 = inputs.perturb(inputs.rng(nx + ny), orc.state(), 0.1)
-    ch.set_state(f0)
-    orc.set_state(f0)
-    ch.step(100)
-    orc.step(100)
-    so = orc.state()
-    # the initial state itself is rounded to 16 bits: one more rounding step
-    assert np.abs(ch.state() - so).max() <= tol16(storage, 101) * dev_scale(so, oracle_mod, drive, value)
+    for launch in (dict(vec=vec, block_x=32, pipeline=1), {}):
+        ch, orc = pair(clb, oracle_mod, nx, ny, 0.3, drive, value, storage=storage, **launch)
+        f0 = inputs.perturb(inputs.rng(nx + ny), orc.state(), 0.1)
+        ch.set_state(f0)
+        orc.set_state(f0)
+        ch.step(100)
+        orc.step(100)
+        so = orc.state()
+        # the initial state itself is rounded to 16 bits: one more rounding step
+        assert np.abs(ch.state() - so).max() <= tol16(storage, 101) * dev_scale(so, oracle_mod, drive, value)
 
 
 # ------------------------------------------- centreline Knudsen number (Sec. 3.2)
