@@ -15,9 +15,12 @@ from dataclasses import dataclass
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "clb_oracle.c")
-_LIB = os.path.join(_HERE, "liboracle_clb.so")
-_LIB_CS = os.path.join(_HERE, "liboracle_clb_cs.so")  # complex-step build
+# Directory holding the C source and the libraries built from it.  The
+# mutation tests point CLB_ORACLE_DIR at a copy with one planted mistake.
+_DIR = os.environ.get("CLB_ORACLE_DIR", _HERE)
+_SRC = os.path.join(_DIR, "clb_oracle.c")
+_LIB = os.path.join(_DIR, "liboracle_clb.so")
+_LIB_CS = os.path.join(_DIR, "liboracle_clb_cs.so")  # complex-step build
 
 _lib = None
 _lib_cs = None

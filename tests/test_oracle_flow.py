@@ -239,3 +239,96 @@ def test_centreline_knudsen_mode_steady_state(oracle_mod):
         out[mode] = o["mass_flow"]
     assert out[1] == pytest.approx(out[0], rel=1e-4)
     assert out[1] != out[0]
+
+
+# ------------------------------------------------------------------ kinematics
+
+@pytest.mark.parametrize("r_b", [0.0, 1.0, 0.37])
+def test_streaming_and_walls_move_populations_by_their_velocity(oracle_mod, r_b):
+    """Kinematics of one streaming step with CBBSR walls (Eq. 5, 20), checked
+    through moments of the whole field rather than population by population.
+    A population that stays in the channel moves by e_i.  One that would cross
+    a wall stays in its row; its bounce-back share r_b stays at its column too,
+    and its specular share 1 - r_b keeps its x velocity, so it moves by e_ix.
+    With k = 2 pi / nx (exact under the periodic wrap in x):
+      sum_x e^{ikx} fbar = sum_nonwall e^{ik(x+e_ix)} f~ + sum_wall [r_b e^{ikx} + (1-r_b) e^{ik(x+e_ix)}] f~
+      sum y fbar         = sum_nonwall (y + e_iy) f~ + sum_wall y f~
+    and mass is unchanged."""
+    nx, ny = 7, 5
+    p = oracle_mod.OracleParams(nx=nx, ny=ny, kn=0.3, r=r_b)
+    s = oracle_mod.OracleSim(p)
+    ft = inputs.rng(int(100 * r_b) + 5).uniform(0.1, 1.0, size=(9, ny, nx))
+    s.set_state(ft)
+    fb = s.prestate()
+    ex, ey = oracle_mod.lattice()
+    X = np.arange(nx)[None, None, :]
+    Y = np.arange(ny)[None, :, None]
+    Ex = ex[:, None, None]
+    Ey = ey[:, None, None]
+    wall = (Y + Ey < 0) | (Y + Ey >= ny)
+    k = 2 * np.pi / nx
+    moved = np.exp(1j * k * (X + Ex))
+    stay = np.exp(1j * k * X)
+    want_x = np.where(wall, r_b * stay + (1 - r_b) * moved, moved)
+    assert (np.exp(1j * k * X) * fb).sum() == pytest.approx((want_x * ft).sum(), abs=1e-13 * ft.sum())
+    want_y = np.where(wall, Y, Y + Ey)
+    assert (Y * fb).sum() == pytest.approx((want_y * ft).sum(), rel=1e-14)
+    assert fb.sum() == pytest.approx(ft.sum(), rel=1e-14)
+
+
+def test_pressure_columns_extrapolate_velocity_linearly(oracle_mod):
+    """Sec. 3.2 names a consistent linear extrapolation at the open ends: the
+    rebuilt end column carries the imposed density and the velocity continued
+    linearly from the two interior neighbours, u_b = 2 u(1) - u(2), whatever
+    the state (the non-equilibrium part adds no mass or momentum)."""
+    nx, ny = 10, 5
+    p = oracle_mod.OracleParams(nx=nx, ny=ny, pressure=True, kn=0.2, rho_in=1.7)
+    s = oracle_mod.OracleSim(p)
+    s.set_state(inputs.perturb(inputs.rng(21), s.state(), 0.2))
+    fb = s.prestate()
+    ex, ey = oracle_mod.lattice()
+    rho = fb.sum(axis=0)
+    ux = np.tensordot(ex, fb, axes=1) / rho
+    uy = np.tensordot(ey, fb, axes=1) / rho
+    for b, i1, i2, rb in ((0, 1, 2, 1.7), (nx - 1, nx - 2, nx - 3, 1.0)):
+        np.testing.assert_allclose(rho[:, b], rb, rtol=1e-14)
+        np.testing.assert_allclose(ux[:, b], 2 * ux[:, i1] - ux[:, i2], rtol=0, atol=1e-14)
+        np.testing.assert_allclose(uy[:, b], 2 * uy[:, i1] - uy[:, i2], rtol=0, atol=1e-14)
+
+
+# ------------------------------------------------------------ continuum limits
+
+@pytest.mark.parametrize("kn", [0.005, 0.01])
+def test_flow_rate_continuum_limit(oracle_mod, kn):
+    """Q of Sec. 3.1 at small Kn: a no-slip Poiseuille flow with the molecular
+    viscosity (Eq. 17 at a = 0) gives Q = sqrt(pi)/(12 Kn) = delta/6, delta =
+    sqrt(pi)/(2 Kn) the rarefaction parameter; slip and the Bosanquet factor
+    add an O(1) amount, close to the linearised-Boltzmann Poiseuille
+    coefficient (about 1.0 for diffuse walls)."""
+    ny = 16
+    _, s = run_periodic(oracle_mod, 2, ny, kn, 1e-7, 12000)
+    q = s.observables()["q_norm"]
+    extra = q - math.sqrt(math.pi) / (12 * kn)
+    assert 0.9 < extra < 1.3, (q, extra)
+
+
+def test_pressure_channel_continuum_limit(oracle_mod):
+    """Pressure-driven channel at Kn_out = 0.02, ratio 1.5, L/H = 50: the
+    isothermal lubrication solution with a pressure-independent viscosity
+    (mean free path inversely proportional to pressure) has p(x)^2 linear in x
+    and mass flow m_ns; slip raises S = m/m_ns a little above 1 and bends p(x)
+    a little less.  So S lies in (1, 1.25) and the centreline pressure follows
+    the no-slip p(x) to within a fifth of that profile's departure from the
+    straight line."""
+    nx, ny, ratio = 401, 8, 1.5
+    p = oracle_mod.OracleParams(nx=nx, ny=ny, pressure=True, kn=0.02, rho_in=ratio)
+    s = oracle_mod.OracleSim(p)
+    s.step(8000, 4)
+    o = s.observables()
+    assert 1.0 < o["q_norm"] < 1.25, o["q_norm"]
+    x = np.arange(nx) / (nx - 1)
+    p_in, p_out = ratio / 3, 1 / 3
+    p_lub = np.sqrt(p_in**2 - (p_in**2 - p_out**2) * x)
+    p_lin = p_in - (p_in - p_out) * x
+    bend = np.abs(p_lub - p_lin).max()
+    assert np.abs(o["p_centre"] - p_lub).max() < 0.2 * bend
