@@ -84,17 +84,21 @@ typedef struct {
      * storages), 1 = direct vector loads with warp shuffles (the only engine
      * that vec and block_x configure), 2..14 = staged through shared memory by
      * TMA bulk copies, tile shape 0..12 of the table in sweep_tma.cu (consumer
-     * threads x nodes per thread, ring stages).  All give bit-identical
-     * results. */
+     * threads x nodes per thread, ring stages), 15..19 = two time steps per
+     * launch with the middle time level kept in a 32-row ring that stays in
+     * L2 (tile shape 0..4 of the table in sweep_pair.cu; an odd last step
+     * runs the single-step TMA sweep of the same shape).  All give
+     * bit-identical results. */
     int pipeline;
     /* Local Knudsen number of a pressure channel (Sec. 3.2): 0 = from the
      * node's own pressure (default), 1 = from the centreline pressure p(x) of
      * the column, taken one step behind (middle row, or mean of the two middle
      * rows).  1 uses the direct-load sweep. */
     int kn_mode;
-    /* Testing only: >= 0 makes the TMA-staged sweep withhold the inputs of
-     * that tile in every step, so that its bounded waits expire and the next
-     * clb_sync / clb_observables returns CLB_ETIMEOUT.  -1 (default) = off. */
+    /* Testing only: >= 0 makes the first TMA-staged sweep launch withhold the
+     * inputs of that tile (single-step engine) or work item (two-step
+     * engine), so that its bounded waits expire and the next clb_sync /
+     * clb_observables returns CLB_ETIMEOUT.  -1 (default) = off. */
     int test_withhold_tile;
 } clb_opts;
 
@@ -171,7 +175,7 @@ typedef struct {
     int storage;          /* clb_storage */
     int vec, block_x;     /* launch shape of the sweep */
     int drive;            /* clb_drive */
-    double bytes_per_node;/* algorithmic bytes moved per node update: 18 * element size */
+    double bytes_per_node;/* algorithmic HBM bytes per node update: 18 * element size (9 + 9 per step; 9 + 9 per two steps with the two-step engine) */
     double sv, sq;        /* s_v, s_q (Eq. 18, 21) at Kn (body force) or Kn_out (pressure) */
     double r;             /* r_b in use */
     double kn, a, g, rho_in, rho_out;

@@ -81,8 +81,11 @@ struct clb_sim {
     size_t col_bytes = 0;
     double* obs = nullptr;  // device scratch of the observable reductions
     unsigned* status = nullptr;  // error bits of bounded device waits
-    int pipeline = 1;       // 1 direct loads, 2.. TMA-staged variants
-    int withhold_tile = -1; // testing: TMA tile whose inputs are withheld
+    int pipeline = 1;       // 1 direct loads, 2..14 TMA-staged variants, 15.. two-step variants
+    void* ring = nullptr;   // two-step engine: the middle time level (kPairRingRows rows)
+    void* pair_ctr = nullptr;  // two-step engine: 2 ny row counters
+    PairArgs pair{};
+    int withhold_tile = -1; // testing: TMA tile (work item) withheld in the first launch
     int kn_mode = 0;        // 1: centreline Knudsen number (pressure channel)
     void* rc = nullptr;     // centreline densities: [2 sides][2 rows][rc_stride], compute type
     int rc_stride = 0;
@@ -427,6 +430,8 @@ clb_status clb_destroy(clb_sim* s) {
     s->dfree(s->obs);
     s->dfree(s->status);
     s->dfree(s->rc);
+    s->dfree(s->ring);
+    s->dfree(s->pair_ctr);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
     delete s;
     return CLB_OK;
@@ -461,8 +466,9 @@ clb_status clb_create(int nx, int ny, double kn, double a, double r, clb_drive d
     int vec = o.vec ? o.vec : (o.storage == CLB_FP64 ? 2 : 4);
     if (!sweep_supported(o.storage, vec)) return fail(CLB_EINVAL, "clb_create: vec = %d not available", vec);
     int block_x = o.block_x ? o.block_x : 128;
-    if (o.pipeline < 0 || o.pipeline > 1 + tma_variant_count())
-        return fail(CLB_EINVAL, "clb_create: pipeline = %d must be 0..%d", o.pipeline, 1 + tma_variant_count());
+    const int max_pipeline = 1 + tma_variant_count() + pair_variant_count();
+    if (o.pipeline < 0 || o.pipeline > max_pipeline)
+        return fail(CLB_EINVAL, "clb_create: pipeline = %d must be 0..%d", o.pipeline, max_pipeline);
     if (o.kn_mode < 0 || o.kn_mode > 1) return fail(CLB_EINVAL, "clb_create: kn_mode = %d must be 0 or 1", o.kn_mode);
     if (block_x < 32 || block_x > 256 || block_x % 32)
         return fail(CLB_EINVAL, "clb_create: block_x = %d must be a multiple of 32 in 32..256", block_x);
@@ -555,6 +561,27 @@ clb_status clb_create(int nx, int ny, double kn, double a, double r, clb_drive d
         clb_destroy(s);
         return fail(CLB_ENOMEM, "clb_create: device allocation of %zu bytes failed", 2 * s->buf_bytes);
     }
+    const int pair_variant = s->pipeline - 2 - tma_variant_count();
+    if (pair_variant >= 0) {
+        PairArgs& p = s->pair;
+        p.ring_rows = kPairRingRows;
+        p.ring_plane = (long long)p.ring_rows * s->pitch;
+        const int mode = drive == CLB_DRIVE_PRESSURE ? MODE_PRESSURE : MODE_PERIODIC;
+        cudaError_t e = plan_sweep_pair(o.storage, mode, pair_variant, nx, &p.tiles_per_row, &p.grid, &p.lag);
+        if (e != cudaSuccess) {
+            clb_destroy(s);
+            return fail(CLB_ECUDA, "clb_create: two-step sweep: %s", cudaGetErrorString(e));
+        }
+        s->ring = s->dalloc((size_t)9 * p.ring_plane * s->elem);
+        s->pair_ctr = s->dalloc((size_t)8 * ny);
+        if (!s->ring || !s->pair_ctr) {
+            clb_destroy(s);
+            return fail(CLB_ENOMEM, "clb_create: device allocation of the two-step ring failed");
+        }
+        p.ring = s->ring;
+        p.done = static_cast<unsigned*>(s->pair_ctr);
+        p.epoch = 0;
+    }
 
     // node-type masks (separable: row type x column type)
     std::vector<uint8_t> rt(ny, 0), ct(s->col_bytes, 0);
@@ -577,6 +604,10 @@ clb_status clb_create(int nx, int ny, double kn, double a, double r, clb_drive d
     chk(cudaMemsetAsync(s->buf[1], 0, s->buf_bytes, s->stream), "memset");
     chk(cudaMemsetAsync(s->obs, 0, s->L.total * sizeof(double), s->stream), "memset");
     chk(cudaMemsetAsync(s->status, 0, sizeof(unsigned), s->stream), "memset");
+    if (s->ring) {
+        chk(cudaMemsetAsync(s->ring, 0, (size_t)9 * s->pair.ring_plane * s->elem, s->stream), "memset");
+        chk(cudaMemsetAsync(s->pair_ctr, 0, (size_t)8 * ny, s->stream), "memset");
+    }
     const double rho_slope = (drive == CLB_DRIVE_PRESSURE) ? (s->rho_out - s->rho_in) / (double)(nx - 1) : 0.0;
     chk(cudaMemsetAsync(s->rc, 0, (size_t)4 * s->rc_stride * (o.storage == CLB_FP64 ? 8 : 4), s->stream), "memset");
     chk(launch_init(s, s->buf[0], s->rho_in, rho_slope), "init");
@@ -596,17 +627,30 @@ clb_status clb_step(clb_sim* s, int64_t n) {
     const int mode = s->drive == CLB_DRIVE_PRESSURE ? MODE_PRESSURE : MODE_PERIODIC;
     SweepArgs a = make_args(s);
     const size_t rc_side = (size_t)2 * s->rc_stride * (s->storage == CLB_FP64 ? 8 : 4);
+    const int pair_variant = s->pipeline - 2 - tma_variant_count();
+    for (; pair_variant >= 0 && n >= 2; n -= 2) {
+        a.fin = s->buf[s->cur];
+        a.fout = s->buf[s->cur ^ 1];
+        cudaError_t e = launch_sweep_pair(s->storage, mode, pair_variant, a, s->pair, s->stream, s->status);
+        if (e != cudaSuccess) return fail(CLB_ECUDA, "clb_step: two-step sweep launch: %s", cudaGetErrorString(e));
+        ++s->pair.epoch;
+        s->cur ^= 1;
+        s->step += 2;
+        s->withhold_tile = a.withhold_tile = -1;  // the testing option acts on the first launch only
+    }
     for (int64_t t = 0; t < n; ++t) {
         a.fin = s->buf[s->cur];
         a.fout = s->buf[s->cur ^ 1];
         a.rc_in = static_cast<const char*>(s->rc) + s->cur * rc_side;
         a.rc_out = static_cast<char*>(s->rc) + (s->cur ^ 1) * rc_side;
+        const int tma_variant = pair_variant >= 0 ? pair_single_variant(pair_variant) : s->pipeline - 2;
         cudaError_t e = s->pipeline >= 2
-                            ? launch_sweep_tma(s->storage, mode, s->pipeline - 2, a, s->stream, s->status)
+                            ? launch_sweep_tma(s->storage, mode, tma_variant, a, s->stream, s->status)
                             : launch_sweep(s->storage, mode, s->vec, s->block_x, a, s->stream);
         if (e != cudaSuccess) return fail(CLB_ECUDA, "clb_step: sweep launch: %s", cudaGetErrorString(e));
         s->cur ^= 1;
         ++s->step;
+        s->withhold_tile = a.withhold_tile = -1;
     }
     return CLB_OK;
 }
@@ -618,6 +662,11 @@ static clb_status check_status(clb_sim* s, const char* who) {
     CUDA_OR(cudaStreamSynchronize(s->stream));
     if (st) {
         CUDA_OR(cudaMemsetAsync(s->status, 0, sizeof(unsigned), s->stream));
+        if (s->pair_ctr) {  // the two-step counters are stale after a launch gave up
+            CUDA_OR(cudaMemsetAsync(s->pair_ctr, 0, (size_t)8 * s->ny, s->stream));
+            CUDA_OR(cudaStreamSynchronize(s->stream));
+            s->pair.epoch = 0;
+        }
         return fail(CLB_ETIMEOUT, "%s: a sweep gave up waiting for its staged inputs (bits %u)", who, st);
     }
     return CLB_OK;
@@ -638,7 +687,9 @@ clb_status clb_info(const clb_sim* s, clb_info_t* info) {
     info->vec = s->vec;
     info->block_x = s->block_x;
     info->drive = s->drive;
-    info->bytes_per_node = 18.0 * (double)s->elem;
+    // HBM bytes per node update: one read and one write of the nine
+    // populations per launch; the two-step engine does two updates per launch
+    info->bytes_per_node = 18.0 * (double)s->elem / (s->ring ? 2.0 : 1.0);
     info->sv = s->sv;
     info->sq = s->sq;
     info->r = s->r;

@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) sweep_kernel(const S
     if (MODE == MODE_PRESSURE) {
         if (kin >= 0) {
             R t[9];
-            rebuild_column<T, R>(a, c, fin, x0 + kin, y, true, t);
+            rebuild_column<T, R>(a, c, Field<T>{fin, a.plane, -1}, x0 + kin, y, true, t);
 #pragma unroll
             for (int k = 0; k < V; ++k)
                 if (k == kin)
@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) sweep_kernel(const S
         }
         if (kout >= 0) {
             R t[9];
-            rebuild_column<T, R>(a, c, fin, x0 + kout, y, false, t);
+            rebuild_column<T, R>(a, c, Field<T>{fin, a.plane, -1}, x0 + kout, y, false, t);
 #pragma unroll
             for (int k = 0; k < V; ++k)
                 if (k == kout)
