@@ -52,6 +52,12 @@ __global__ void __launch_bounds__(NC + 32, MB) sweep_tma_kernel(const SweepArgs 
         fence_barrier_init();
     }
     __syncthreads();
+    // Programmatic dependent launch: the next sweep may begin launching now
+    // (its blocks start as this one's leave their SMs); no global memory is
+    // touched before the previous sweep has completed and its writes are
+    // visible, so reading its output and overwriting its input are safe.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 
     const int my_tiles = ntiles > (int)blockIdx.x ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
@@ -116,8 +122,17 @@ cudaError_t launch_tma_one(const SweepArgs& a, cudaStream_t st, unsigned* status
     const int tiles_per_row = (a.nx + G::W - 1) / G::W;
     const int ntiles = tiles_per_row * a.ny;
     const int grid = min(ntiles, max(1, per_sm) * sms);
-    kern<<<grid, NC + 32, G::SMEM, st>>>(a, ntiles, tiles_per_row, status);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(NC + 32);
+    cfg.dynamicSmemBytes = G::SMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, a, ntiles, tiles_per_row, status);
 }
 
 }  // namespace
