@@ -55,7 +55,19 @@ __device__ __forceinline__ float rcp(float x) {
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
-__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+// FP64 reciprocal by Newton-Raphson: the approximate hardware reciprocal
+// (rcp.approx.ftz.f64) refined twice by r <- r + r (1 - x r), each step
+// squaring the relative error, which ends within a few ulp of 1/x for the
+// positive normal densities and rate denominators it is applied to.  GB300's
+// FP64 rate is low, so this is cheaper than a correctly rounded division.
+__device__ __forceinline__ double rcp(double x) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    double e = fma(-x, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-x, r, 1.0);
+    return fma(r, e, r);
+}
 
 // The launch constants of the compute type, read in place from the kernel
 // parameters.

@@ -214,38 +214,44 @@ template <class T>
 __global__ void __launch_bounds__(kObsCols* kObsRows)
     obs_kernel(const T* f, double* obs, ObsLayout L, int nx, int ny, int pitch, int xoff, long long plane,
                double ref0, double ref_slope, double gx, double gy, int prof_col, double isc) {
+    // Per node in the storage's compute type (FP32 for FP32/16-bit storage,
+    // whose values carry FP32 or coarser rounding already; FP64 for FP64),
+    // accumulated across nodes in FP64.  The mass flow needs no division:
+    // rho u_x = sum_i e_ix f~_i - rho F_x / 2.
+    using R = RT<T>;
     __shared__ double sh[5][kObsRows][kObsCols];
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int x = blockIdx.x * kObsCols + tx;
     double m = 0, us = 0, mass = 0, rc = 0, bad = 0;
     if (x < nx) {
         const double ref = ref0 + ref_slope * x;
+        const R hgx = R(0.5 * gx), hgy = R(0.5 * gy);
         for (int y = ty; y < ny; y += kObsRows) {
             const T* row = f + (long long)y * pitch + xoff + x;
-            double drho = 0, jx = 0, jy = 0;
+            R v[9];
 #pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                const double v = (double)Codec<T>::dec(row[i * plane], RT<T>(isc));
-                drho += v;
-                jx += c_ex[i] * v;
-                jy += c_ey[i] * v;
-            }
-            const double rho = ref + drho;
-            const double ux = (jx - 0.5 * rho * gx) / rho;
-            const double uy = (jy - 0.5 * rho * gy) / rho;
+            for (int i = 0; i < 9; ++i) v[i] = Codec<T>::dec(row[i * plane], R(isc));
+            const R a57 = v[5] - v[7], a86 = v[8] - v[6];
+            const R drho = v[0] + (v[1] + v[3]) + (v[2] + v[4]) + ((v[5] + v[7]) + (v[6] + v[8]));
+            const R rho = R(ref) + drho;
+            const R mx = (v[1] - v[3]) + (a57 + a86) - hgx * rho;  // rho u_x
+            const R my = (v[2] - v[4]) + (a57 - a86) - hgy * rho;  // rho u_y
+            const R irho = rcp(rho);
+            const R ux = mx * irho, uy = my * irho;
             if (!isfinite(rho) || !isfinite(ux) || !isfinite(uy)) bad += 1;
-            m += rho * ux;
-            us += ux;
-            mass += rho;
+            const double rho_d = ref + (double)drho;
+            m += (double)mx;
+            us += (double)ux;
+            mass += rho_d;
             // centreline: the middle row, or the mean of the two middle rows
             if (ny & 1) {
-                if (y == (ny - 1) / 2) rc += rho;
+                if (y == (ny - 1) / 2) rc += rho_d;
             } else if (y == ny / 2 - 1 || y == ny / 2) {
-                rc += 0.5 * rho;
+                rc += 0.5 * rho_d;
             }
             if (x == prof_col) {
-                obs[L.prof_x + y] = ux;
-                obs[L.prof_y + y] = uy;
+                obs[L.prof_x + y] = (double)ux;
+                obs[L.prof_y + y] = (double)uy;
             }
         }
     }
