@@ -48,7 +48,8 @@ typedef enum {
     CLB_ENOMEM = 2,   /* device or host allocation failed */
     CLB_ECUDA = 3,    /* a CUDA call failed (message has the CUDA error) */
     CLB_ENUMERIC = 4, /* a NaN or Inf was seen in the fields */
-    CLB_ETIMEOUT = 5  /* a bounded device wait gave up (TMA-staged sweep); the results are invalid */
+    CLB_ETIMEOUT = 5, /* a bounded device wait gave up (TMA-staged sweep); the results are invalid */
+    CLB_EIO = 6       /* a checkpoint file could not be written or read, or is not a valid checkpoint */
 } clb_status;
 
 typedef enum {
@@ -195,6 +196,40 @@ clb_status clb_destroy(clb_sim* sim);
 
 /* Message for the last failing call on this thread ("" if none). */
 const char* clb_last_error(void);
+
+/* ------------------------------------------------------------------------
+ * Checkpoint and resume.  The paper has no counterpart; a long run (the
+ * steady states of Sec. 3.2 take 1e5-1e6 steps) can stop and continue
+ * unchanged.
+ *
+ * clb_save writes the channel's complete state to the file `path`
+ * (created or replaced):
+ *   - the problem statement (nx, ny, drive and its value, Kn, a, r_b in use,
+ *     B2, sigma, s3, s8, rho_out, storage, kn_mode);
+ *   - the step counter and the residual history of clb_observables;
+ *   - the stored populations of the current time level, bit for bit in the
+ *     storage format, halo columns included;
+ *   - the centreline densities that the next step's rates use (kn_mode 1).
+ * The layout is a 176-byte little-endian header, then the two payloads.  The
+ * header holds the magic "CLBCKPT1", the version and the payload sizes, and a
+ * 64-bit FNV-1a checksum over the payloads.  clb_save synchronises the stream.
+ * The file is only as portable as the byte order: same-endian machines only.
+ * Errors: CLB_EINVAL (NULL argument); CLB_ETIMEOUT (an earlier sweep gave
+ * up, nothing written); CLB_ECUDA; CLB_EIO (the file cannot be written).
+ *
+ * clb_load creates a simulation from such a file.  Everything that defines
+ * the problem comes from the file, including opts->storage, kn_mode, b2,
+ * sigma, s3, s8 and rho_out, which are ignored.  Only the run-time options
+ * are taken from `opts` (NULL = defaults): stream, allocator hooks, pipeline,
+ * vec, block_x.  Stepping the loaded simulation gives, bit for bit, what
+ * stepping the saved one would have given (every sweep engine computes the
+ * same values).
+ * Errors: CLB_EINVAL (NULL path or out); CLB_EIO (unreadable, truncated, bad
+ * magic, version or checksum, or a layout this build would not create);
+ * CLB_ENOMEM / CLB_ECUDA as for clb_create.  *out is NULL on failure.
+ * ------------------------------------------------------------------------ */
+clb_status clb_save(clb_sim* sim, const char* path);
+clb_status clb_load(const char* path, const clb_opts* opts, clb_sim** out);
 
 /* ------------------------------------------------------------------------
  * Batched Knudsen sweep (Sec. 3.1, Fig. 2): many periodic body-force channels

@@ -19,7 +19,7 @@ import numpy as np
 
 from . import build as _build
 
-CLB_OK, CLB_EINVAL, CLB_ENOMEM, CLB_ECUDA, CLB_ENUMERIC, CLB_ETIMEOUT = range(6)
+CLB_OK, CLB_EINVAL, CLB_ENOMEM, CLB_ECUDA, CLB_ENUMERIC, CLB_ETIMEOUT, CLB_EIO = range(7)
 CLB_DRIVE_BODY_FORCE, CLB_DRIVE_PRESSURE = 0, 1
 CLB_FP64, CLB_FP32_SHIFTED, CLB_FP16_SCALED, CLB_BF16_SCALED = 0, 1, 2, 3
 
@@ -90,6 +90,8 @@ def _load():
     lib.clb_destroy.argtypes = [P]
     lib.clb_last_error.argtypes = []
     lib.clb_last_error.restype = C.c_char_p
+    lib.clb_save.argtypes = [P, C.c_char_p]
+    lib.clb_load.argtypes = [C.c_char_p, C.POINTER(clb_opts), C.POINTER(P)]
     lib.clb_observables_noalloc.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
                                             C.c_double, C.c_int, P, C.POINTER(clb_scalars), D, D, D, D, D]
     I = C.POINTER(C.c_int)
@@ -107,7 +109,8 @@ def _load():
     lib.clb_adjoint_backward.argtypes = [P, C.c_double, D]
     lib.clb_adjoint_destroy.argtypes = [P]
     for name in ("clb_create", "clb_step", "clb_observables", "clb_get_state", "clb_set_state",
-                 "clb_info", "clb_sync", "clb_destroy", "clb_observables_noalloc", "clb_batch_create",
+                 "clb_info", "clb_sync", "clb_destroy", "clb_save", "clb_load", "clb_observables_noalloc",
+                 "clb_batch_create",
                  "clb_batch_step", "clb_batch_tune", "clb_batch_observables", "clb_batch_get_state",
                  "clb_batch_set_state", "clb_batch_info", "clb_batch_destroy", "clb_adjoint_forward",
                  "clb_adjoint_backward", "clb_adjoint_destroy"):
@@ -189,6 +192,16 @@ def clb_destroy(sim):
     return _check(lib.clb_destroy(sim))
 
 
+def clb_save(sim, path):
+    return _check(lib.clb_save(sim, os.fsencode(path)))
+
+
+def clb_load(path, opts: clb_opts | None = None):
+    h = C.c_void_p()
+    _check(lib.clb_load(os.fsencode(path), C.byref(opts) if opts is not None else None, C.byref(h)))
+    return h
+
+
 # ------------------------------------------------------------ convenience
 
 class Channel:
@@ -207,6 +220,18 @@ class Channel:
         import torch
 
         self.nx, self.ny = int(nx), int(ny)
+        o = self._runtime_opts(stream, vec, block_x, pipeline, torch_allocator, alloc_hook)
+        o.b2, o.sigma, o.s3, o.s8, o.rho_out = b2, sigma, s3, s8, rho_out
+        o.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+        o.kn_mode = int(kn_mode)
+        o.test_withhold_tile = int(test_withhold_tile)
+        d = DRIVE[drive] if isinstance(drive, str) else int(drive)
+        self.sim = clb_create(nx, ny, kn, a, r, d, drive_value, o)
+
+    def _runtime_opts(self, stream, vec, block_x, pipeline, torch_allocator, alloc_hook) -> clb_opts:
+        """Options that do not define the problem: stream, engine, allocator."""
+        import torch
+
         dev = torch.cuda.current_device()
         # a stream of its own by default; the legacy default stream (handle 0)
         # cannot be handed over, because NULL asks the library for its own stream
@@ -214,12 +239,8 @@ class Channel:
             stream = torch.cuda.Stream(dev)
         self._stream = stream
         o = clb_opts_default()
-        o.b2, o.sigma, o.s3, o.s8, o.rho_out = b2, sigma, s3, s8, rho_out
-        o.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
         o.vec, o.block_x = int(vec), int(block_x)
         o.pipeline = int(pipeline)
-        o.kn_mode = int(kn_mode)
-        o.test_withhold_tile = int(test_withhold_tile)
         o.stream = C.c_void_p(self._stream.cuda_stream)
         if torch_allocator:
             s = self._stream
@@ -237,8 +258,22 @@ class Channel:
 
             self._hooks = (ALLOC_FN(_alloc), FREE_FN(_free))
             o.alloc, o.free = self._hooks
-        d = DRIVE[drive] if isinstance(drive, str) else int(drive)
-        self.sim = clb_create(nx, ny, kn, a, r, d, drive_value, o)
+        return o
+
+    def save(self, path) -> None:
+        """Checkpoint the channel to a file (clb_save)."""
+        clb_save(self.sim, path)
+
+    @classmethod
+    def load(cls, path, stream=None, vec=0, block_x=0, pipeline=0, torch_allocator=True, alloc_hook=None):
+        """A channel resumed from a checkpoint file (clb_load); the problem
+        comes from the file, the engine and stream from the arguments."""
+        ch = cls.__new__(cls)
+        o = ch._runtime_opts(stream, vec, block_x, pipeline, torch_allocator, alloc_hook)
+        ch.sim = clb_load(path, o)
+        i = clb_info(ch.sim)
+        ch.nx, ch.ny = i.nx, i.ny
+        return ch
 
     def close(self):
         if getattr(self, "sim", None):

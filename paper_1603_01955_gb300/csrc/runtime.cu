@@ -43,7 +43,6 @@ constexpr double kPi = 3.14159265358979323846;
 __constant__ double c_w[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
                               1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
 __constant__ int c_ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
-__constant__ int c_ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 
 // Observable scratch layout (doubles): per-column m(x), centre rho(x), column
 // sums of u_x, profile u_x(y), u_y(y), then per-block partial sums.
@@ -101,6 +100,7 @@ struct clb_sim {
     double sv = 0, sq = 0;
     double ref0 = 0, ref_slope = 0;
     double store_scale = 1;  // 16-bit formats: stored value = deviation * store_scale
+    double drive_value = 0;  // as given to clb_create (G, or p_in/p_out)
     int64_t step = 0;
     bool have_prev = false;
     double prev_mass_flow = 0;
@@ -501,6 +501,7 @@ clb_status clb_create(int nx, int ny, double kn, double a, double r, clb_drive d
     s->yc0 = (ny % 2) ? (ny - 1) / 2 : ny / 2 - 1;
     s->yc1 = (ny % 2) ? s->yc0 : ny / 2;
     s->drive = drive;
+    s->drive_value = drive_value;
     s->kn = kn;
     s->a = a;
     s->b2 = o.b2;
@@ -939,5 +940,146 @@ extern "C" clb_status clb_observables_noalloc(const double* f_dev, int nx, int n
     if (part[3] > 0)
         return fail(CLB_ENUMERIC, "clb_observables_noalloc: %.0f nodes with a non-finite density or velocity",
                     part[3]);
+    return CLB_OK;
+}
+
+// ----------------------------------------------------------- checkpoints
+
+namespace {
+
+struct CkptHeader {
+    char magic[8];           // "CLBCKPT1"
+    uint32_t version;        // 1
+    uint32_t header_bytes;   // sizeof(CkptHeader)
+    int32_t nx, ny, drive, storage, kn_mode, pitch, elem, rc_stride;
+    int64_t step;
+    int32_t have_prev, reserved0;
+    double kn, a, r, drive_value, b2, sigma, s3, s8, rho_out, prev_mass_flow;
+    uint64_t buf_bytes, rc_bytes;  // payloads: stored populations, centreline densities
+    uint64_t checksum;             // FNV-1a 64 over the payloads in that order
+    uint64_t reserved1;
+};
+static_assert(sizeof(CkptHeader) == 176, "checkpoint header layout");
+constexpr char kCkptMagic[8] = {'C', 'L', 'B', 'C', 'K', 'P', 'T', '1'};
+
+uint64_t fnv1a(const std::vector<unsigned char>& v, uint64_t h) {
+    for (unsigned char b : v) h = (h ^ b) * 1099511628211ull;
+    return h;
+}
+constexpr uint64_t kFnvOffset = 14695981039346656037ull;
+
+size_t rc_side_bytes(int rc_stride, int storage) {
+    return (size_t)2 * rc_stride * (storage == CLB_FP64 ? 8 : 4);
+}
+
+}  // namespace
+
+clb_status clb_save(clb_sim* s, const char* path) {
+    if (!s || !path) return fail(CLB_EINVAL, "clb_save: NULL argument");
+    clb_status st = check_status(s, "clb_save");  // synchronises; refuses results of a failed sweep
+    if (st != CLB_OK) return st;
+    const size_t rc_side = rc_side_bytes(s->rc_stride, s->storage);
+    std::vector<unsigned char> buf(s->buf_bytes), rc(rc_side);
+    CUDA_OR(cudaMemcpyAsync(buf.data(), s->buf[s->cur], s->buf_bytes, cudaMemcpyDeviceToHost, s->stream));
+    CUDA_OR(cudaMemcpyAsync(rc.data(), static_cast<const char*>(s->rc) + s->cur * rc_side, rc_side,
+                            cudaMemcpyDeviceToHost, s->stream));
+    CUDA_OR(cudaStreamSynchronize(s->stream));
+    CkptHeader h;
+    std::memset(&h, 0, sizeof h);
+    std::memcpy(h.magic, kCkptMagic, sizeof h.magic);
+    h.version = 1;
+    h.header_bytes = sizeof h;
+    h.nx = s->nx;
+    h.ny = s->ny;
+    h.drive = s->drive;
+    h.storage = s->storage;
+    h.kn_mode = s->kn_mode;
+    h.pitch = s->pitch;
+    h.elem = (int32_t)s->elem;
+    h.rc_stride = s->rc_stride;
+    h.step = s->step;
+    h.have_prev = s->have_prev ? 1 : 0;
+    h.kn = s->kn;
+    h.a = s->a;
+    h.r = s->r;
+    h.drive_value = s->drive_value;
+    h.b2 = s->b2;
+    h.sigma = s->sigma;
+    h.s3 = s->s3;
+    h.s8 = s->s8;
+    h.rho_out = s->rho_out;
+    h.prev_mass_flow = s->prev_mass_flow;
+    h.buf_bytes = buf.size();
+    h.rc_bytes = rc.size();
+    h.checksum = fnv1a(rc, fnv1a(buf, kFnvOffset));
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(CLB_EIO, "clb_save: cannot open %s for writing", path);
+    const bool ok = std::fwrite(&h, sizeof h, 1, f) == 1 && std::fwrite(buf.data(), 1, buf.size(), f) == buf.size() &&
+                    std::fwrite(rc.data(), 1, rc.size(), f) == rc.size();
+    if (std::fclose(f) != 0 || !ok) return fail(CLB_EIO, "clb_save: writing %s failed", path);
+    return CLB_OK;
+}
+
+clb_status clb_load(const char* path, const clb_opts* opts, clb_sim** out) {
+    g_err[0] = 0;
+    if (!path || !out) return fail(CLB_EINVAL, "clb_load: NULL argument");
+    *out = nullptr;
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(CLB_EIO, "clb_load: cannot open %s", path);
+    CkptHeader h;
+    std::vector<unsigned char> buf, rc;
+    const char* why = nullptr;
+    if (std::fread(&h, sizeof h, 1, f) != 1) {
+        why = "truncated header";
+    } else if (std::memcmp(h.magic, kCkptMagic, sizeof h.magic) != 0) {
+        why = "not a CLB checkpoint";
+    } else if (h.version != 1 || h.header_bytes != sizeof h) {
+        why = "unsupported checkpoint version";
+    } else if (h.storage < CLB_FP64 || h.storage > CLB_BF16_SCALED || h.nx < 1 || h.ny < 1 || h.ny > 65535 ||
+               h.pitch < h.nx || h.elem != (h.storage == CLB_FP64 ? 8 : h.storage == CLB_FP32_SHIFTED ? 4 : 2) ||
+               h.buf_bytes != (uint64_t)9 * h.ny * h.pitch * h.elem || h.rc_stride < h.nx ||
+               h.rc_bytes != rc_side_bytes(h.rc_stride, h.storage)) {
+        why = "inconsistent header";
+    } else {
+        buf.resize(h.buf_bytes);
+        rc.resize(h.rc_bytes);
+        if (std::fread(buf.data(), 1, buf.size(), f) != buf.size() || std::fread(rc.data(), 1, rc.size(), f) != rc.size())
+            why = "truncated payload";
+        else if (fnv1a(rc, fnv1a(buf, kFnvOffset)) != h.checksum)
+            why = "checksum mismatch";
+    }
+    std::fclose(f);
+    if (why) return fail(CLB_EIO, "clb_load: %s: %s", path, why);
+
+    clb_opts o;
+    clb_opts_default(&o);
+    if (opts) o = *opts;
+    o.storage = h.storage;
+    o.kn_mode = h.kn_mode;
+    o.b2 = h.b2;
+    o.sigma = h.sigma;
+    o.s3 = h.s3;
+    o.s8 = h.s8;
+    o.rho_out = h.rho_out;
+    clb_sim* s = nullptr;
+    clb_status st = clb_create(h.nx, h.ny, h.kn, h.a, h.r, (clb_drive)h.drive, h.drive_value, &o, &s);
+    if (st != CLB_OK) return st;
+    if (s->pitch != h.pitch || (int)s->elem != h.elem || s->rc_stride != h.rc_stride || s->buf_bytes != h.buf_bytes) {
+        clb_destroy(s);
+        return fail(CLB_EIO, "clb_load: %s: layout differs from what this build creates", path);
+    }
+    cudaError_t e = cudaMemcpyAsync(s->buf[s->cur], buf.data(), buf.size(), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(static_cast<char*>(s->rc) + s->cur * rc.size(), rc.data(), rc.size(),
+                            cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) {
+        clb_destroy(s);
+        return fail(CLB_ECUDA, "clb_load: %s", cudaGetErrorString(e));
+    }
+    s->step = h.step;
+    s->have_prev = h.have_prev != 0;
+    s->prev_mass_flow = h.prev_mass_flow;
+    *out = s;
     return CLB_OK;
 }
