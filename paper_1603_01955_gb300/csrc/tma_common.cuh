@@ -167,8 +167,24 @@ __device__ __forceinline__ void tile_update(const SweepArgs& a, const KC<typenam
     using R = typename Codec<T>::R;
     constexpr int E = 16 / (int)sizeof(T);
     constexpr bool kShift = (MODE == MODE_PRESSURE) && !std::is_same<T, double>::value;
+    // The thread's window of slot i, columns x0 - 1 .. x0 + V (index k + 1):
+    // the V middle values in one aligned vector load, an end value only for the
+    // slots that pull from it (e_x = +1 from the left, e_x = -1 from the right;
+    // the wall rows pull slots 5-8 from both sides).
+    using VT = typename VecT<T, V>::type;
+    R w[9][V + 2];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const T* p = stage + i * SEG + E + sv;
+        const VT v = *reinterpret_cast<const VT*>(p);
+        const T* e = reinterpret_cast<const T*>(&v);
+#pragma unroll
+        for (int k = 0; k < V; ++k) w[i][k + 1] = Codec<T>::dec(e[k], c.isc);
+        w[i][0] = (i == 1 || i >= 5) ? Codec<T>::dec(p[-1], c.isc) : R(0);
+        w[i][V + 1] = (i == 3 || i >= 5) ? Codec<T>::dec(p[V], c.isc) : R(0);
+    }
     // element of slot i at column x0 + k (k may be -1 .. V)
-    auto at = [&](int i, int k) -> R { return Codec<T>::dec(stage[i * SEG + E + sv + k], c.isc); };
+    auto at = [&](int i, int k) -> R { return w[i][k + 1]; };
     R f[9][V];
 #pragma unroll
     for (int k = 0; k < V; ++k) {
