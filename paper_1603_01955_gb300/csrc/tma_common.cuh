@@ -112,6 +112,23 @@ template <> struct VecT<__half, 2> { using type = unsigned int; };
 template <> struct VecT<__nv_bfloat16, 4> { using type = uint2; };
 template <> struct VecT<__nv_bfloat16, 2> { using type = unsigned int; };
 
+// Pairs of 16-bit values converted by one instruction each way.
+template <class T> struct Pair16 {
+    static constexpr bool ok = false;
+};
+template <> struct Pair16<__half> {
+    static constexpr bool ok = true;
+    using P = __half2;
+    static __device__ __forceinline__ float2 dec(P p) { return __half22float2(p); }
+    static __device__ __forceinline__ P enc(float a, float b) { return __floats2half2_rn(a, b); }
+};
+template <> struct Pair16<__nv_bfloat16> {
+    static constexpr bool ok = true;
+    using P = __nv_bfloat162;
+    static __device__ __forceinline__ float2 dec(P p) { return __bfloat1622float2(p); }
+    static __device__ __forceinline__ P enc(float a, float b) { return __floats2bfloat162_rn(a, b); }
+};
+
 template <class T, int NC, int V, int S> struct Geometry {
     static constexpr int W = NC * V;                    // columns per tile
     static constexpr int E = 16 / (int)sizeof(T);       // halo elements per side
@@ -178,8 +195,18 @@ __device__ __forceinline__ void tile_update(const SweepArgs& a, const KC<typenam
         const T* p = stage + i * SEG + E + sv;
         const VT v = *reinterpret_cast<const VT*>(p);
         const T* e = reinterpret_cast<const T*>(&v);
+        if constexpr (Pair16<T>::ok && V % 2 == 0) {
+            // two 16-bit values per conversion (exact, as the scalar one)
 #pragma unroll
-        for (int k = 0; k < V; ++k) w[i][k + 1] = Codec<T>::dec(e[k], c.isc);
+            for (int k = 0; k < V; k += 2) {
+                const float2 q = Pair16<T>::dec(reinterpret_cast<const typename Pair16<T>::P*>(e)[k / 2]);
+                w[i][k + 1] = Codec<T>::unscale(q.x, c.isc);
+                w[i][k + 2] = Codec<T>::unscale(q.y, c.isc);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < V; ++k) w[i][k + 1] = Codec<T>::dec(e[k], c.isc);
+        }
         w[i][0] = (i == 1 || i >= 5) ? Codec<T>::dec(p[-1], c.isc) : R(0);
         w[i][V + 1] = (i == 3 || i >= 5) ? Codec<T>::dec(p[V], c.isc) : R(0);
     }
@@ -268,14 +295,21 @@ __device__ __forceinline__ void tile_update(const SweepArgs& a, const KC<typenam
     const long long P = dst_plane;
     T* orow = dst + (long long)(y & dst_rmask) * a.pitch + a.xoff;
     if (x0 + V <= a.nx) {
-        using VT = typename VecT<T, V>::type;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            VT w;
-            T* e = reinterpret_cast<T*>(&w);
+            VT v;
+            T* e = reinterpret_cast<T*>(&v);
+            if constexpr (Pair16<T>::ok && V % 2 == 0) {
+                // two values per conversion, each rounded as by the scalar one
 #pragma unroll
-            for (int k = 0; k < V; ++k) e[k] = Codec<T>::enc(f[i][k], c.sc);
-            *reinterpret_cast<VT*>(orow + i * P + x0) = w;
+                for (int k = 0; k < V; k += 2)
+                    reinterpret_cast<typename Pair16<T>::P*>(e)[k / 2] =
+                        Pair16<T>::enc(Codec<T>::prescale(f[i][k], c.sc), Codec<T>::prescale(f[i][k + 1], c.sc));
+            } else {
+#pragma unroll
+                for (int k = 0; k < V; ++k) e[k] = Codec<T>::enc(f[i][k], c.sc);
+            }
+            *reinterpret_cast<VT*>(orow + i * P + x0) = v;
         }
     } else {
 #pragma unroll
