@@ -225,8 +225,9 @@ const char* clb_last_error(void);
  * stepping the saved one would have given (every sweep engine computes the
  * same values).
  * Errors: CLB_EINVAL (NULL path or out); CLB_EIO (unreadable, truncated, bad
- * magic, version or checksum, or a layout this build would not create);
- * CLB_ENOMEM / CLB_ECUDA as for clb_create.  *out is NULL on failure.
+ * magic, version or checksum, or a layout this library version would not
+ * create); CLB_ENOMEM / CLB_ECUDA as for clb_create.  *out is NULL on
+ * failure.
  * ------------------------------------------------------------------------ */
 clb_status clb_save(clb_sim* sim, const char* path);
 clb_status clb_load(const char* path, const clb_opts* opts, clb_sim** out);

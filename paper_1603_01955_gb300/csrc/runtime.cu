@@ -1066,7 +1066,7 @@ clb_status clb_load(const char* path, const clb_opts* opts, clb_sim** out) {
     if (st != CLB_OK) return st;
     if (s->pitch != h.pitch || (int)s->elem != h.elem || s->rc_stride != h.rc_stride || s->buf_bytes != h.buf_bytes) {
         clb_destroy(s);
-        return fail(CLB_EIO, "clb_load: %s: layout differs from what this build creates", path);
+        return fail(CLB_EIO, "clb_load: %s: layout differs from what this library version creates", path);
     }
     cudaError_t e = cudaMemcpyAsync(s->buf[s->cur], buf.data(), buf.size(), cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess)
