@@ -424,6 +424,7 @@ clb_status clb_adjoint_destroy(clb_adjoint* h) {
 
 clb_status clb_adjoint_forward(int nx, int ny, double kn, double a, double r, double g, int64_t nsteps,
                                int checkpoint_every, const clb_opts* opts, clb_adjoint** out, double* J) {
+    clb::TraceRange trace_("clb_adjoint_forward");
     if (!out) return (clb_status)set_error(CLB_EINVAL, "clb_adjoint_forward: out is NULL");
     *out = nullptr;
     clb_opts o;
@@ -501,6 +502,7 @@ clb_status clb_adjoint_forward(int nx, int ny, double kn, double a, double r, do
 }
 
 clb_status clb_adjoint_backward(clb_adjoint* h, double seed, double grad[3]) {
+    clb::TraceRange trace_("clb_adjoint_backward");
     if (!h || !grad) return (clb_status)set_error(CLB_EINVAL, "clb_adjoint_backward: NULL argument");
     cudaError_t e = h->storage == CLB_FP64 ? backward_run<double>(h, seed, grad) : backward_run<float>(h, seed, grad);
     if (e != cudaSuccess) return (clb_status)set_error(CLB_ECUDA, "clb_adjoint_backward: %s", cudaGetErrorString(e));

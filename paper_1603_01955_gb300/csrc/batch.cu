@@ -459,6 +459,7 @@ clb_status clb_batch_tune(clb_batch* b, int* block_out) {
 }
 
 clb_status clb_batch_step(clb_batch* b, int64_t n) {
+    clb::TraceRange trace_("clb_batch_step");
     if (!b || n < 0) return (clb_status)set_error(CLB_EINVAL, "clb_batch_step: bad arguments");
     if (!b->tuned) {
         clb_status st = clb_batch_tune(b, nullptr);

@@ -4,6 +4,7 @@
 
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 namespace clb {
 
@@ -77,6 +78,15 @@ void rates_at(double kn, int ny, double a, double b2, double* sv, double* sq);
 
 // r_b of Eq. 21 from the TMAC sigma, with B1 = 1 - 0.1817 sigma (Sec. 3).
 double r_from_sigma(double sigma);
+
+// NVTX range over a host call of the library (Nsight timelines show the
+// calls; without an attached tool the push and pop return at once).
+struct TraceRange {
+    explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange&) = delete;
+    TraceRange& operator=(const TraceRange&) = delete;
+};
 
 // Record a failure message for clb_last_error() and return st.
 int set_error(int st, const char* fmt, ...);

@@ -629,6 +629,7 @@ clb_status clb_create(int nx, int ny, double kn, double a, double r, clb_drive d
 }
 
 clb_status clb_step(clb_sim* s, int64_t n) {
+    clb::TraceRange trace_("clb_step");
     if (!s) return fail(CLB_EINVAL, "clb_step: sim is NULL");
     if (n < 0) return fail(CLB_EINVAL, "clb_step: n < 0");
     const int mode = s->drive == CLB_DRIVE_PRESSURE ? MODE_PRESSURE : MODE_PERIODIC;
@@ -713,6 +714,7 @@ clb_status clb_info(const clb_sim* s, clb_info_t* info) {
 }
 
 clb_status clb_get_state(clb_sim* s, double* host_f) {
+    clb::TraceRange trace_("clb_get_state");
     if (!s || !host_f) return fail(CLB_EINVAL, "clb_get_state: NULL argument");
     const long long n = 9LL * s->nx * s->ny;
     double* tmp = static_cast<double*>(s->dalloc(n * sizeof(double)));
@@ -733,6 +735,7 @@ clb_status clb_get_state(clb_sim* s, double* host_f) {
 }
 
 clb_status clb_set_state(clb_sim* s, const double* host_f) {
+    clb::TraceRange trace_("clb_set_state");
     if (!s || !host_f) return fail(CLB_EINVAL, "clb_set_state: NULL argument");
     const long long n = 9LL * s->nx * s->ny;
     double* tmp = static_cast<double*>(s->dalloc(n * sizeof(double)));
@@ -759,6 +762,7 @@ clb_status clb_set_state(clb_sim* s, const double* host_f) {
 
 clb_status clb_observables(clb_sim* s, int profile_col, clb_scalars* sc, double* ux_prof, double* uy_prof,
                            double* p_centre, double* dp_nonlin, double* m_of_x) {
+    clb::TraceRange trace_("clb_observables");
     if (!s) return fail(CLB_EINVAL, "clb_observables: sim is NULL");
     const int nx = s->nx, ny = s->ny;
     if (profile_col < 0 || profile_col >= nx) profile_col = (s->drive == CLB_DRIVE_PRESSURE) ? nx - 1 : 0;
@@ -975,6 +979,7 @@ size_t rc_side_bytes(int rc_stride, int storage) {
 }  // namespace
 
 clb_status clb_save(clb_sim* s, const char* path) {
+    clb::TraceRange trace_("clb_save");
     if (!s || !path) return fail(CLB_EINVAL, "clb_save: NULL argument");
     clb_status st = check_status(s, "clb_save");  // synchronises; refuses results of a failed sweep
     if (st != CLB_OK) return st;
@@ -1021,6 +1026,7 @@ clb_status clb_save(clb_sim* s, const char* path) {
 }
 
 clb_status clb_load(const char* path, const clb_opts* opts, clb_sim** out) {
+    clb::TraceRange trace_("clb_load");
     g_err[0] = 0;
     if (!path || !out) return fail(CLB_EINVAL, "clb_load: NULL argument");
     *out = nullptr;
