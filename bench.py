@@ -310,6 +310,7 @@ def run_gpu(args):
     }
     if not args.no_batch:
         line["knudsen_sweep"] = knudsen_sweep_bench(clb, torch, args.batch_steps)
+        line["small_channel"] = small_channel_bench(clb, torch, args.batch_steps)
     if args.no_cpu_baseline or world > 1:
         line["cpu_baseline"] = None
     else:
@@ -370,6 +371,34 @@ def knudsen_sweep_bench(clb, torch, steps):
         "steps": steps,
         "q_min_kn_after_steps": kn[i],
     }
+
+
+def small_channel_bench(clb, torch, steps):
+    """The 1601 x 16 pressure channel of Sec. 3.2 (L/H = 100, Kn_out = 0.1,
+    ratio 2, FP32-shifted): each sweep takes a few microseconds, so launch
+    overhead bounds it; MLUPS with the sweeps replayed from CUDA graphs in
+    chunks of 64 and with one launch per step."""
+    c = {"nx": 1601, "ny": 16, "kn_out": 0.1, "ratio": 2.0}
+    nodes = c["nx"] * c["ny"]
+    out = {"workload": "pressure channel 1601 x 16 (25,616 nodes), Kn_out 0.1, p_in/p_out 2, fp32s",
+           "nodes": nodes, "steps": steps}
+    for name, graph_steps in (("graphs", 64), ("launches", -1)):
+        ch = clb.Channel(c["nx"], c["ny"], c["kn_out"], drive="pressure", drive_value=c["ratio"], storage="fp32s",
+                         graph_steps=graph_steps)
+        ch.step(256)
+        ch.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ch.stream)
+        ch.step(steps)
+        e1.record(ch.stream)
+        e1.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        ch.sync()
+        ch.close()
+        out[f"mlups_{name}"] = round(nodes * steps / t / 1e6, 1)
+        out[f"us_per_step_{name}"] = round(t / steps * 1e6, 3)
+    out["speedup"] = round(out["mlups_graphs"] / out["mlups_launches"], 2)
+    return out
 
 
 def errors_vs_oracle(clb, variants, ref, steps):
@@ -529,7 +558,8 @@ def main():
                     help="oracle steps of the CPU baseline (also the step count of the error report)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variants", default="fp32s,fp64,fp16s,bf16s", help="storages to time (fp32s first)")
-    ap.add_argument("--no-batch", action="store_true", help="skip the batched Knudsen-sweep measurement")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the launch-bound measurements (batched Knudsen sweep, 1601x16 channel)")
     ap.add_argument("--batch-steps", type=int, default=20000)
     ap.add_argument("--pipeline", type=int, default=0,
                     help="sweep engine for FP32/16-bit storage (clb_opts.pipeline; 0 = library default)")

@@ -101,6 +101,13 @@ typedef struct {
      * engine), so that its bounded waits expire and the next clb_sync /
      * clb_observables returns CLB_ETIMEOUT.  -1 (default) = off. */
     int test_withhold_tile;
+    /* CUDA-graph replay of clb_step for channels whose sweeps are short
+     * enough for launch overhead to matter: chunks of this many consecutive
+     * sweeps are captured once (per buffer parity) and replayed.  0 =
+     * default (64 for channels below 2^20 nodes, off above; off with the
+     * two-step engine and the testing option), < 0 = off, > 0 = chunk length.
+     * Results are identical with or without replay. */
+    int graph_steps;
 } clb_opts;
 
 void clb_opts_default(clb_opts* opts);

@@ -35,7 +35,7 @@ class clb_opts(C.Structure):
         ("b2", C.c_double), ("sigma", C.c_double), ("s3", C.c_double), ("s8", C.c_double),
         ("rho_out", C.c_double), ("storage", C.c_int), ("vec", C.c_int), ("block_x", C.c_int),
         ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
-        ("pipeline", C.c_int), ("kn_mode", C.c_int), ("test_withhold_tile", C.c_int),
+        ("pipeline", C.c_int), ("kn_mode", C.c_int), ("test_withhold_tile", C.c_int), ("graph_steps", C.c_int),
     ]
 
 
@@ -216,11 +216,11 @@ class Channel:
 
     def __init__(self, nx, ny, kn, a=2.0, r=-1.0, drive="body_force", drive_value=0.0, storage="fp32s",
                  vec=0, block_x=0, b2=0.55, sigma=1.0, s3=1.1, s8=1.2, rho_out=1.0, stream=None,
-                 torch_allocator=True, pipeline=0, kn_mode=0, test_withhold_tile=-1, alloc_hook=None):
+                 torch_allocator=True, pipeline=0, kn_mode=0, test_withhold_tile=-1, alloc_hook=None, graph_steps=0):
         import torch
 
         self.nx, self.ny = int(nx), int(ny)
-        o = self._runtime_opts(stream, vec, block_x, pipeline, torch_allocator, alloc_hook)
+        o = self._runtime_opts(stream, vec, block_x, pipeline, torch_allocator, alloc_hook, graph_steps)
         o.b2, o.sigma, o.s3, o.s8, o.rho_out = b2, sigma, s3, s8, rho_out
         o.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
         o.kn_mode = int(kn_mode)
@@ -228,8 +228,8 @@ class Channel:
         d = DRIVE[drive] if isinstance(drive, str) else int(drive)
         self.sim = clb_create(nx, ny, kn, a, r, d, drive_value, o)
 
-    def _runtime_opts(self, stream, vec, block_x, pipeline, torch_allocator, alloc_hook) -> clb_opts:
-        """Options that do not define the problem: stream, engine, allocator."""
+    def _runtime_opts(self, stream, vec, block_x, pipeline, torch_allocator, alloc_hook, graph_steps=0) -> clb_opts:
+        """Options that do not define the problem: stream, engine, allocator, graph replay."""
         import torch
 
         dev = torch.cuda.current_device()
@@ -241,6 +241,7 @@ class Channel:
         o = clb_opts_default()
         o.vec, o.block_x = int(vec), int(block_x)
         o.pipeline = int(pipeline)
+        o.graph_steps = int(graph_steps)
         o.stream = C.c_void_p(self._stream.cuda_stream)
         if torch_allocator:
             s = self._stream
@@ -265,11 +266,12 @@ class Channel:
         clb_save(self.sim, path)
 
     @classmethod
-    def load(cls, path, stream=None, vec=0, block_x=0, pipeline=0, torch_allocator=True, alloc_hook=None):
+    def load(cls, path, stream=None, vec=0, block_x=0, pipeline=0, torch_allocator=True, alloc_hook=None,
+             graph_steps=0):
         """A channel resumed from a checkpoint file (clb_load); the problem
         comes from the file, the engine and stream from the arguments."""
         ch = cls.__new__(cls)
-        o = ch._runtime_opts(stream, vec, block_x, pipeline, torch_allocator, alloc_hook)
+        o = ch._runtime_opts(stream, vec, block_x, pipeline, torch_allocator, alloc_hook, graph_steps)
         ch.sim = clb_load(path, o)
         i = clb_info(ch.sim)
         ch.nx, ch.ny = i.nx, i.ny

@@ -85,6 +85,8 @@ struct clb_sim {
     void* pair_ctr = nullptr;  // two-step engine: 2 ny row counters
     PairArgs pair{};
     int withhold_tile = -1; // testing: TMA tile (work item) withheld in the first launch
+    int graph_steps = 0;    // sweeps per replayed CUDA graph (0: no replay); even
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};  // per parity of `cur` at the chunk start
     int kn_mode = 0;        // 1: centreline Knudsen number (pressure channel)
     void* rc = nullptr;     // centreline densities: [2 sides][2 rows][rc_stride], compute type
     int rc_stride = 0;
@@ -438,6 +440,8 @@ clb_status clb_destroy(clb_sim* s) {
     s->dfree(s->rc);
     s->dfree(s->ring);
     s->dfree(s->pair_ctr);
+    for (cudaGraphExec_t g : s->graph)
+        if (g) cudaGraphExecDestroy(g);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
     delete s;
     return CLB_OK;
@@ -498,6 +502,16 @@ clb_status clb_create(int nx, int ny, double kn, double a, double r, clb_drive d
         s->pipeline = o.pipeline;
     else
         s->pipeline = (o.storage == CLB_FP32_SHIFTED) ? 14 : 3;
+    {
+        // graph replay: not with the two-step engine (cooperative launches) or the testing option
+        int k = 0;
+        if (o.graph_steps > 0)
+            k = o.graph_steps;
+        else if (o.graph_steps == 0)
+            k = ((long long)nx * ny < (1LL << 20)) ? 64 : 0;
+        if (s->pipeline > 1 + tma_variant_count() || o.test_withhold_tile >= 0) k = 0;
+        s->graph_steps = k + (k & 1);  // even: a chunk ends on the buffer it started from
+    }
     s->yc0 = (ny % 2) ? (ny - 1) / 2 : ny / 2 - 1;
     s->yc1 = (ny % 2) ? s->yc0 : ny / 2;
     s->drive = drive;
@@ -628,13 +642,44 @@ clb_status clb_create(int nx, int ny, double kn, double a, double r, clb_drive d
     return CLB_OK;
 }
 
+// One single-step sweep launch from buffer `cur` (direct or TMA engine).
+static cudaError_t launch_single(clb_sim* s, SweepArgs& a, int mode, int cur) {
+    const size_t rc_side = (size_t)2 * s->rc_stride * (s->storage == CLB_FP64 ? 8 : 4);
+    const int pair_variant = s->pipeline - 2 - tma_variant_count();
+    a.fin = s->buf[cur];
+    a.fout = s->buf[cur ^ 1];
+    a.rc_in = static_cast<const char*>(s->rc) + cur * rc_side;
+    a.rc_out = static_cast<char*>(s->rc) + (cur ^ 1) * rc_side;
+    const int tma_variant = pair_variant >= 0 ? pair_single_variant(pair_variant) : s->pipeline - 2;
+    return s->pipeline >= 2 ? launch_sweep_tma(s->storage, mode, tma_variant, a, s->stream, s->status)
+                            : launch_sweep(s->storage, mode, s->vec, s->block_x, a, s->stream);
+}
+
+// Capture graph_steps consecutive sweeps starting from buffer `cur` into an
+// executable graph (programmatic launch edges are kept).
+static cudaError_t build_graph(clb_sim* s, const SweepArgs& base, int mode, int cur, cudaGraphExec_t* out) {
+    SweepArgs a = base;
+    cudaError_t e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return e;
+    cudaError_t le = cudaSuccess;
+    for (int k = 0; k < s->graph_steps && le == cudaSuccess; ++k, cur ^= 1) le = launch_single(s, a, mode, cur);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(s->stream, &g);
+    if (le != cudaSuccess || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return le != cudaSuccess ? le : e;
+    }
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    return e;
+}
+
 clb_status clb_step(clb_sim* s, int64_t n) {
     clb::TraceRange trace_("clb_step");
     if (!s) return fail(CLB_EINVAL, "clb_step: sim is NULL");
     if (n < 0) return fail(CLB_EINVAL, "clb_step: n < 0");
     const int mode = s->drive == CLB_DRIVE_PRESSURE ? MODE_PRESSURE : MODE_PERIODIC;
     SweepArgs a = make_args(s);
-    const size_t rc_side = (size_t)2 * s->rc_stride * (s->storage == CLB_FP64 ? 8 : 4);
     const int pair_variant = s->pipeline - 2 - tma_variant_count();
     for (; pair_variant >= 0 && n >= 2; n -= 2) {
         a.fin = s->buf[s->cur];
@@ -646,15 +691,18 @@ clb_status clb_step(clb_sim* s, int64_t n) {
         s->step += 2;
         s->withhold_tile = a.withhold_tile = -1;  // the testing option acts on the first launch only
     }
+    // replayed chunks (the chunk length is even, so `cur` is where it started)
+    for (; s->graph_steps > 0 && n >= s->graph_steps; n -= s->graph_steps) {
+        if (!s->graph[s->cur]) {
+            cudaError_t e = build_graph(s, a, mode, s->cur, &s->graph[s->cur]);
+            if (e != cudaSuccess) return fail(CLB_ECUDA, "clb_step: capturing the sweep graph: %s", cudaGetErrorString(e));
+        }
+        cudaError_t e = cudaGraphLaunch(s->graph[s->cur], s->stream);
+        if (e != cudaSuccess) return fail(CLB_ECUDA, "clb_step: graph launch: %s", cudaGetErrorString(e));
+        s->step += s->graph_steps;
+    }
     for (int64_t t = 0; t < n; ++t) {
-        a.fin = s->buf[s->cur];
-        a.fout = s->buf[s->cur ^ 1];
-        a.rc_in = static_cast<const char*>(s->rc) + s->cur * rc_side;
-        a.rc_out = static_cast<char*>(s->rc) + (s->cur ^ 1) * rc_side;
-        const int tma_variant = pair_variant >= 0 ? pair_single_variant(pair_variant) : s->pipeline - 2;
-        cudaError_t e = s->pipeline >= 2
-                            ? launch_sweep_tma(s->storage, mode, tma_variant, a, s->stream, s->status)
-                            : launch_sweep(s->storage, mode, s->vec, s->block_x, a, s->stream);
+        cudaError_t e = launch_single(s, a, mode, s->cur);
         if (e != cudaSuccess) return fail(CLB_ECUDA, "clb_step: sweep launch: %s", cudaGetErrorString(e));
         s->cur ^= 1;
         ++s->step;
