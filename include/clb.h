@@ -81,9 +81,10 @@ typedef struct {
     void (*free)(void* ptr, void* ctx);
     void* alloc_ctx;
     /* How the sweep reads its inputs (FP32 and 16-bit storage; FP64 and
-     * kn_mode 1 always 1): 0 = default (14 for FP32_SHIFTED, 3 for the 16-bit
-     * storages), 1 = direct vector loads with warp shuffles (the only engine
-     * that vec and block_x configure), 2..14 = staged through shared memory by
+     * kn_mode 1 always 1): 0 = default (1 for channels below 2^20 nodes;
+     * larger ones 14 for FP32_SHIFTED, 3 for the 16-bit storages), 1 = direct
+     * vector loads with warp shuffles (the only engine that vec and block_x
+     * configure), 2..14 = staged through shared memory by
      * TMA bulk copies, tile shape 0..12 of the table in sweep_tma.cu (consumer
      * threads x nodes per thread, ring stages), 15..19 = two time steps per
      * launch with the middle time level kept in a 32-row ring that stays in

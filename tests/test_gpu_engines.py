@@ -86,6 +86,10 @@ def test_two_step_many_launches(clb, storage, nx, ny, drive):
 @pytest.mark.parametrize("storage,kn_mode,want", [("fp64", 0, 1), ("fp32s", 0, 14), ("fp16s", 0, 3),
                                                   ("bf16s", 0, 3), ("fp32s", 1, 1)])
 def test_default_engine(clb, storage, kn_mode, want):
-    ch = clb.Channel(40, 4, 0.2, drive="pressure", drive_value=1.5, storage=storage, kn_mode=kn_mode)
+    """TMA shapes for channels of 2^20 nodes and more, the direct sweep below."""
+    ch = clb.Channel(4097, 256, 0.2, drive="pressure", drive_value=1.5, storage=storage, kn_mode=kn_mode)
     assert ch.info()["pipeline"] == want
     ch.close()
+    small = clb.Channel(4095, 256, 0.2, drive="pressure", drive_value=1.5, storage=storage, kn_mode=kn_mode)
+    assert small.info()["pipeline"] == 1
+    small.close()
