@@ -256,7 +256,7 @@ __device__ void gather_node(const SweepArgs& a, const KC<R>& c, const Field<T> f
         const T* p = f.base + i * f.plane + (long long)((y + dy) & f.rmask) * a.pitch + a.xoff + xx;
         return Codec<T>::dec(ld_field<kCG>(p), c.isc);
     };
-    const int rt = a.row_type[y];
+    const int rt = row_kind(y, a.ny);
     const R sha = c.sha, shd = c.shd;  // source at x-1; the source at x+1 gets the negative
     o[0] = at(0, 0, x);
     o[1] = at(1, 0, x - 1) + sha;

@@ -17,6 +17,12 @@ enum : uint8_t { ROW_BOTTOM = 1, ROW_TOP = 2 };
 // the halo columns -1 and nx so that the next sweep needs no wrap-around.
 enum : uint8_t { COL_INLET = 1, COL_OUTLET = 2, COL_HALO_RIGHT = 4, COL_HALO_LEFT = 8 };
 
+// The row_type bits of row y, from the index alone (the same bits the row
+// mask holds); kernels that walk rows compute them instead of loading them.
+__host__ __device__ __forceinline__ int row_kind(int y, int ny) {
+    return (y == 0 ? ROW_BOTTOM : 0) | (y == ny - 1 ? ROW_TOP : 0);
+}
+
 // Launch constants in the compute type of a sweep, derived on the host so
 // that no thread spends FP64 instructions on them (GB300's FP64 rate is a
 // small fraction of its FP32 rate).

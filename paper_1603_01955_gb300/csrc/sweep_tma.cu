@@ -60,12 +60,24 @@ __global__ void __launch_bounds__(NC + 32, MB) sweep_tma_kernel(const SweepArgs 
     asm volatile("griddepcontrol.wait;" ::: "memory");
 
     const int my_tiles = ntiles > (int)blockIdx.x ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    // Tile blockIdx.x + it * gridDim.x sits at row y, column tile xt; both
+    // advance by the grid's quotient and remainder, with no division per tile.
+    const int y_step = (int)gridDim.x / tiles_per_row, xt_step = (int)gridDim.x % tiles_per_row;
+    auto advance = [&](int& y, int& xt) {
+        xt += xt_step;
+        y += y_step;
+        if (xt >= tiles_per_row) {
+            xt -= tiles_per_row;
+            ++y;
+        }
+    };
 
     if (threadIdx.x >= NC) {
         // ---------------------------------------------------------- producer
         if (threadIdx.x != NC) return;
         int issued = 0;
-        for (int it = 0; it < my_tiles; ++it) {
+        int y = (int)blockIdx.x / tiles_per_row, xt = (int)blockIdx.x % tiles_per_row;
+        for (int it = 0; it < my_tiles; ++it, advance(y, xt)) {
             const int s = it % S;
             if (it >= S && !mbar_wait(empty + s, ((it / S) - 1) & 1)) {
                 atomicOr(status, 1u);
@@ -73,11 +85,9 @@ __global__ void __launch_bounds__(NC + 32, MB) sweep_tma_kernel(const SweepArgs 
                 break;
             }
             if (*(volatile int*)&abort_flag) break;
-            const int tile = (int)blockIdx.x + it * (int)gridDim.x;
-            if (tile == a.withhold_tile) continue;  // testing: the consumers' waits must expire
-            const int y = tile / tiles_per_row;
-            const int x0 = (tile % tiles_per_row) * G::W;
-            load_tile<T, G::SEG>(a, src, y, x0, a.row_type[y], smem + s * G::STAGE_BYTES, full + s);
+            if ((int)blockIdx.x + it * (int)gridDim.x == a.withhold_tile)
+                continue;  // testing: the consumers' waits must expire
+            load_tile<T, G::SEG>(a, src, y, xt * G::W, smem + s * G::STAGE_BYTES, full + s);
             issued = it + 1;
         }
         // copies still in flight for stages nobody will consume: wait (bounded)
@@ -88,18 +98,16 @@ __global__ void __launch_bounds__(NC + 32, MB) sweep_tma_kernel(const SweepArgs 
 
     // -------------------------------------------------------------- consumers
     const int tcx = threadIdx.x;
-    for (int it = 0; it < my_tiles; ++it) {
+    int y = (int)blockIdx.x / tiles_per_row, xt = (int)blockIdx.x % tiles_per_row;
+    for (int it = 0; it < my_tiles; ++it, advance(y, xt)) {
         const int s = it % S;
         if (!mbar_wait(full + s, (it / S) & 1)) {
             atomicOr(status, 2u);
             abort_flag = 1;
             return;
         }
-        const int tile = (int)blockIdx.x + it * (int)gridDim.x;
-        const int y = tile / tiles_per_row;
-        const int x0 = (tile % tiles_per_row) * G::W + tcx * V;
         const T* stage = reinterpret_cast<const T*>(smem + s * G::STAGE_BYTES);
-        tile_update<T, MODE, V, G::SEG, false>(a, c, stage, tcx * V, x0, y, a.row_type[y], empty + s, src, fout,
+        tile_update<T, MODE, V, G::SEG, false>(a, c, stage, tcx * V, xt * G::W + tcx * V, y, empty + s, src, fout,
                                                a.plane, -1);
     }
 }

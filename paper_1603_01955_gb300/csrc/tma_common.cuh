@@ -155,9 +155,10 @@ __device__ __forceinline__ int seg_dy(int i, int rt) {
 // Issue the nine bulk copies of the tile starting at column x0 of row y from
 // field f into `stage`, completing on `full` (one arrive with the byte count).
 template <class T, int SEG>
-__device__ __forceinline__ void load_tile(const SweepArgs& a, const Field<T> f, int y, int x0, int rt,
+__device__ __forceinline__ void load_tile(const SweepArgs& a, const Field<T> f, int y, int x0,
                                           unsigned char* stage, uint64_t* full) {
     constexpr int E = 16 / (int)sizeof(T);
+    const int rt = row_kind(y, a.ny);
     // the segment starts E columns left of the tile; clip at the row end
     const long long first = (long long)a.xoff + x0 - E;
     const int n_el = (int)min((long long)SEG, (long long)a.pitch - first);
@@ -170,7 +171,9 @@ __device__ __forceinline__ void load_tile(const SweepArgs& a, const Field<T> f, 
 }
 
 // One consumer thread's share of a staged tile: nodes x0 .. x0+V-1 of row y
-// (x0 = tile start + thread * V).  Pulls the populations out of the stage
+// (x0 = tile start + thread * V).  The row's wall bits and the columns' inlet,
+// outlet and halo roles follow from the indices (x = 0 and x = nx - 1; y = 0
+// and y = ny - 1), so no mask is loaded.  Pulls the populations out of the stage
 // (slot i holds the plane direction i is pulled from, sv the thread's offset
 // in it), applies the CBBSR walls (Eq. 20) and the shift of the deviation
 // storage, releases the stage on `empty`, rebuilds pressure columns from the
@@ -179,9 +182,10 @@ __device__ __forceinline__ void load_tile(const SweepArgs& a, const Field<T> f, 
 // kCG: `src` was written earlier in the same launch.
 template <class T, int MODE, int V, int SEG, bool kCG>
 __device__ __forceinline__ void tile_update(const SweepArgs& a, const KC<typename Codec<T>::R>& c, const T* stage,
-                                            int sv, int x0, int y, int rt, uint64_t* empty, const Field<T> src,
+                                            int sv, int x0, int y, uint64_t* empty, const Field<T> src,
                                             T* dst, long long dst_plane, int dst_rmask) {
     using R = typename Codec<T>::R;
+    const int rt = row_kind(y, a.ny);
     constexpr int E = 16 / (int)sizeof(T);
     constexpr bool kShift = (MODE == MODE_PRESSURE) && !std::is_same<T, double>::value;
     // The thread's window of slot i, columns x0 - 1 .. x0 + V (index k + 1):
@@ -252,17 +256,11 @@ __device__ __forceinline__ void tile_update(const SweepArgs& a, const KC<typenam
     mbar_arrive(empty);  // the stage's data is in registers now
     if (x0 >= a.nx) return;
 
-    uint8_t ct[V];
-    int kin = -1, kout = -1;
-#pragma unroll
-    for (int k = 0; k < V; ++k) {
-        ct[k] = a.col_type[x0 + k];
-        if (MODE == MODE_PRESSURE) {
-            if (ct[k] & COL_INLET) kin = k;
-            if (ct[k] & COL_OUTLET) kout = k;
-        }
-    }
+    // the thread's node in the first and in the last column, if any (x0 < nx)
+    const int kfirst = x0 == 0 ? 0 : -1;
+    const int klast = a.nx - 1 - x0 < V ? a.nx - 1 - x0 : -1;
     if (MODE == MODE_PRESSURE) {
+        const int kin = kfirst, kout = klast;  // inlet x = 0, outlet x = nx - 1
         if (kin >= 0) {
             R t[9];
             rebuild_column<T, R, kCG>(a, c, src, x0 + kin, y, true, t);
@@ -319,14 +317,15 @@ __device__ __forceinline__ void tile_update(const SweepArgs& a, const KC<typenam
                 for (int i = 0; i < 9; ++i) orow[i * P + x0 + k] = Codec<T>::enc(f[i][k], c.sc);
     }
     if (MODE == MODE_PERIODIC) {
+        // column 0 is mirrored into the halo column nx, column nx - 1 into -1
 #pragma unroll
         for (int k = 0; k < V; ++k) {
-            if (ct[k] & COL_HALO_RIGHT) {
+            if (k == kfirst) {
                 orow[3 * P + a.nx] = Codec<T>::enc(f[3][k], c.sc);
                 orow[6 * P + a.nx] = Codec<T>::enc(f[6][k], c.sc);
                 orow[7 * P + a.nx] = Codec<T>::enc(f[7][k], c.sc);
             }
-            if (ct[k] & COL_HALO_LEFT) {
+            if (k == klast) {
                 orow[1 * P - 1] = Codec<T>::enc(f[1][k], c.sc);
                 orow[5 * P - 1] = Codec<T>::enc(f[5][k], c.sc);
                 orow[8 * P - 1] = Codec<T>::enc(f[8][k], c.sc);
