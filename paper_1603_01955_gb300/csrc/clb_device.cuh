@@ -11,6 +11,8 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "clb_internal.h"
 
 namespace clb {
@@ -34,10 +36,10 @@ template <> struct Codec<float> {
 // convert two values per instruction.
 template <> struct Codec<__half> {
     using R = float;
-    static __device__ __forceinline__ float unscale(float v, float isc) { return v * isc; }
-    static __device__ __forceinline__ float prescale(float v, float sc) { return v * sc; }
-    static __device__ __forceinline__ float dec(__half v, float isc) { return __half2float(v) * isc; }
-    static __device__ __forceinline__ __half enc(float v, float sc) { return __float2half_rn(v * sc); }
+    static __device__ __forceinline__ float unscale(float v, float isc) { return __fmul_rn(v, isc); }
+    static __device__ __forceinline__ float prescale(float v, float sc) { return __fmul_rn(v, sc); }
+    static __device__ __forceinline__ float dec(__half v, float isc) { return __fmul_rn(__half2float(v), isc); }
+    static __device__ __forceinline__ __half enc(float v, float sc) { return __float2half_rn(__fmul_rn(v, sc)); }
 };
 // BF16 has FP32's exponent range, so its values are stored unscaled (scale 1).
 template <> struct Codec<__nv_bfloat16> {
@@ -126,104 +128,202 @@ __device__ __forceinline__ void macro_dev(const R d[9], R& drho, R& jx, R& jy) {
     jy = (d[2] - d[4]) + (p57 - p86);
 }
 
+// Lane arithmetic of the collision.  Every operation is written out with its
+// rounding (no multiply-add is left for the compiler to contract), so a node
+// gets the same bits whether it is collided alone (float, double) or together
+// with its neighbour in packed FP32 (float2: the f32x2 instructions of
+// sm_100-class GPUs add, multiply or fused-multiply-add both halves of a
+// register pair at once, each half rounded as the scalar operation).  Other
+// number types (the dual numbers of the adjoint) use their operators.
+namespace ln {
+__device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+// Packed FP32 in inline PTX: the .rn forms are never fused by the compiler.
+#define CLB_F32X2_BINARY(NAME, OP)                                                  \
+    __device__ __forceinline__ float2 NAME(float2 a, float2 b) {                    \
+        float2 r;                                                                   \
+        asm("{\n\t.reg .b64 pa, pb, pr;\n\t"                                       \
+            "mov.b64 pa, {%2, %3};\n\t"                                             \
+            "mov.b64 pb, {%4, %5};\n\t" OP                                           \
+            " pr, pa, pb;\n\t"                                                       \
+            "mov.b64 {%0, %1}, pr;\n\t}"                                             \
+            : "=f"(r.x), "=f"(r.y)                                                    \
+            : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));                                \
+        return r;                                                                   \
+    }
+CLB_F32X2_BINARY(add, "add.rn.f32x2")
+CLB_F32X2_BINARY(sub, "sub.rn.f32x2")
+CLB_F32X2_BINARY(mul, "mul.rn.f32x2")
+#undef CLB_F32X2_BINARY
+__device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) {
+    float2 r;
+    asm("{\n\t.reg .b64 pa, pb, pc, pr;\n\t"
+        "mov.b64 pa, {%2, %3};\n\t"
+        "mov.b64 pb, {%4, %5};\n\t"
+        "mov.b64 pc, {%6, %7};\n\t"
+        "fma.rn.f32x2 pr, pa, pb, pc;\n\t"
+        "mov.b64 {%0, %1}, pr;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return r;
+}
+template <class L> __device__ __forceinline__ L add(L a, L b) { return a + b; }
+template <class L> __device__ __forceinline__ L sub(L a, L b) { return a - b; }
+template <class L> __device__ __forceinline__ L mul(L a, L b) { return a * b; }
+template <class L> __device__ __forceinline__ L fma(L a, L b, L c) { return a * b + c; }
+// a scalar in every lane
+template <class L, class S> __device__ __forceinline__ L bc(S s) {
+    if constexpr (std::is_same<L, float2>::value)
+        return make_float2(float(s), float(s));
+    else
+        return L(s);
+}
+}  // namespace ln
+
+__device__ __forceinline__ float2 rcp(float2 a) { return make_float2(rcp(a.x), rcp(a.y)); }
+
 // One cascaded collision (Eq. 4 with Eq. 6-9, 12-13), in place on the
 // deviations d relative to R = ref.  MODE_PERIODIC: body force F, constant
 // rates.  MODE_PRESSURE: no force, s_v and s_q from the local Knudsen number
 // Kn = Kn_out rho_out / rho (Sec. 3.2) through Eq. 18 and Eq. 21.
 // rho_kn (pressure channel, optional): the density that sets the local
 // Knudsen number when it is not the node's own (the column's centreline).
-template <typename R, int MODE>
-__device__ __forceinline__ void collide(R (&d)[9], R ref, const KC<R>& c, const R* rho_kn = nullptr) {
+// L: the lane type, R (one node) or float2 (two FP32 nodes, lane x the first).
+//
+// The order of operations is fixed: no product is ever an operand of an add
+// or a subtract (a product that is summed is a fused multiply-add, ln::fma,
+// or is formed with a zero addend, prod), so no compiler can fuse it
+// differently for one lane type than for another, and each node gets the same
+// bits alone or packed.  A few of Eq. 7's braces are regrouped for fewer
+// operations; each regrouping is stated where it is made.
+template <typename R, int MODE, class L = R>
+__device__ __forceinline__ void collide(L (&d)[9], L ref, const KC<R>& c, const L* rho_kn = nullptr) {
+    using namespace ln;
+    auto k = [](double v) { return bc<L>(R(v)); };          // a literal in every lane
+    auto prod = [&](L a, L b) { return fma(a, b, k(0.0)); };  // a product that is summed later
     // raw moments of Eq. 8 (deviation parts)
-    const R a57 = d[5] + d[7], a68 = d[6] + d[8];
-    const R p57 = d[5] - d[7], p86 = d[8] - d[6];
-    const R kxy = a57 - a68;
-    const R kxxyy = a57 + a68;
-    const R kxxy = p57 - p86;
-    const R kxyy = p57 + p86;
-    const R s13 = d[1] + d[3], s24 = d[2] + d[4];
-    const R kxx = s13 + kxxyy;
-    const R kyy = s24 + kxxyy;
-    const R drho = d[0] + s13 + s24 + kxxyy;
-    const R jx = (d[1] - d[3]) + kxyy;
-    const R jy = (d[2] - d[4]) + kxxy;
+    const L a57 = add(d[5], d[7]), a68 = add(d[6], d[8]);
+    const L p57 = sub(d[5], d[7]), p86 = sub(d[8], d[6]);
+    const L nkxy = sub(a68, a57);  // -k'_xy
+    const L kxxyy = add(a57, a68);
+    const L kxxy = sub(p57, p86);
+    const L kxyy = add(p57, p86);
+    const L s13 = add(d[1], d[3]), s24 = add(d[2], d[4]);
+    const L kxx = add(s13, kxxyy);
+    const L kyy = add(s24, kxxyy);
+    const L drho = add(add(add(d[0], s13), s24), kxxyy);
+    const L jx = add(sub(d[1], d[3]), kxyy);
+    const L jy = add(sub(d[2], d[4]), kxxy);
     // Eq. 12-13
-    const R rho = ref + drho;
-    const R irho = rcp(rho);
-    R ux = jx * irho, uy = jy * irho;
+    const L rho = add(ref, drho);
+    const L irho = rcp(rho);
+    L ux, uy;
     if (MODE == MODE_PERIODIC) {
-        ux += c.hfx;
-        uy += c.hfy;
-    }
-    // relaxation rates
-    R sv4, sq4;
-    if (MODE == MODE_PRESSURE) {
-        // tau = A/q, q = rho + B; 1/s_v = 1/2 + tau (Eq. 18);
-        // 1/s_q = 1/2 + 3/(16 tau) + (pi B2/4) tau (Eq. 21)
-        const R q = (rho_kn ? *rho_kn : rho) + c.B;
-        sv4 = R(0.25) * q * rcp(R(0.5) * q + c.A);
-        sq4 = R(0.25) * q * rcp(q * (R(0.5) + c.A316 * q) + c.CA);
+        ux = fma(jx, irho, bc<L>(c.hfx));
+        uy = fma(jy, irho, bc<L>(c.hfy));
     } else {
-        sv4 = c.sv_4;
-        sq4 = c.sq_4;
+        ux = mul(jx, irho);
+        uy = mul(jy, irho);
     }
-    const R ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
-    const R third = R(1.0 / 3.0) * ref;
-    const R kxxf = third + kxx;  // full k'_xx
-    const R kyyf = third + kyy;  // full k'_yy
-    // Eq. 7, in cascade order
-    R t3 = R(2.0 / 3.0) * drho - (kxx + kyy) + rho * (ux2 + uy2);
-    R t4 = rho * (ux2 - uy2) - (kxx - kyy);
-    R t5 = rho * uxy - kxy;
-    R t6 = R(2) * rho * ux2 * uy + kxxy - R(2) * ux * kxy - uy * kxxf;
-    R t7 = R(2) * rho * ux * uy2 + kxyy - R(2) * uy * kxy - ux * kyyf;
-    R t8 = R(1.0 / 9.0) * drho + R(3) * rho * ux2 * uy2 -
-           (kxxyy - R(2) * ux * kxyy - R(2) * uy * kxxy + ux2 * kyyf + uy2 * kxxf + R(4) * uxy * kxy);
+    // relaxation rates: tau = A/q, q = rho + B; s_v/4 = (q/4) / (q/2 + A)
+    // (Eq. 18); s_q/4 = (q/4) / (q (1/2 + 3q/(16A)) + (pi B2/4) A) (Eq. 21)
+    L sv4, sq4;
+    if (MODE == MODE_PRESSURE) {
+        const L q = add(rho_kn ? *rho_kn : rho, bc<L>(c.B));
+        const L q4 = mul(q, k(0.25));
+        sv4 = mul(q4, rcp(fma(q, k(0.5), bc<L>(c.A))));
+        sq4 = mul(q4, rcp(fma(q, fma(bc<L>(c.A316), q, k(0.5)), bc<L>(c.CA))));
+    } else {
+        sv4 = bc<L>(c.sv_4);
+        sq4 = bc<L>(c.sq_4);
+    }
+    const L ux2 = mul(ux, ux), uy2 = mul(uy, uy), uxy = mul(ux, uy);
+    const L nux = mul(k(-1.0), ux), nuy = mul(k(-1.0), uy);
+    const L ux_2 = mul(k(2.0), ux), uy_2 = mul(k(2.0), uy);
+    const L nux_2 = mul(k(-2.0), ux), nuy_2 = mul(k(-2.0), uy);
+    const L kxxf = fma(k(1.0 / 3.0), ref, kxx);  // full k'_xx
+    const L kyyf = fma(k(1.0 / 3.0), ref, kyy);  // full k'_yy
+    // Eq. 7, in cascade order.  t5u = rho ux uy - k'_xy is the xy brace
+    // without its force term; the xxy, xyy and xxyy braces are written through
+    // it: 2 rho ux^2 uy - 2 ux k'_xy = 2 ux t5u, 2 rho ux uy^2 - 2 uy k'_xy =
+    // 2 uy t5u, and 3 rho ux^2 uy^2 - 4 ux uy k'_xy = ux uy (3 t5u - k'_xy).
+    const L t5u = fma(rho, uxy, nkxy);
+    L t3 = sub(fma(rho, fma(ux, ux, uy2), mul(k(2.0 / 3.0), drho)), add(kxx, kyy));
+    L t4 = fma(rho, fma(nuy, uy, ux2), sub(kyy, kxx));
+    L t5 = t5u;
+    L t6 = fma(ux_2, t5u, fma(nuy, kxxf, kxxy));
+    L t7 = fma(uy_2, t5u, fma(nux, kyyf, kxyy));
+    L t8 = sub(fma(uy_2, kxxy, fma(ux_2, kxyy, fma(uxy, fma(k(3.0), t5u, nkxy), mul(k(1.0 / 9.0), drho)))),
+               fma(ux2, kyyf, fma(uy2, kxxf, kxxyy)));
     if (MODE == MODE_PERIODIC) {
-        const R fx = c.fx, fy = c.fy;
-        t3 -= rho * (fx * ux + fy * uy);
-        t4 -= rho * (fx * ux - fy * uy);
-        t5 -= R(0.5) * rho * (fx * uy + fy * ux);
-        t6 -= R(0.5) * rho * (fy * ux2 + R(2) * fx * uxy);
-        t7 -= R(0.5) * rho * (fx * uy2 + R(2) * fy * uxy);
-        t8 -= rho * (fx * ux * uy2 + fy * uy * ux2);
+        const L fx = bc<L>(c.fx), fy = bc<L>(c.fy);
+        const L nrho = sub(k(0.0), rho), nrh = mul(k(0.5), nrho);
+        t3 = fma(nrho, fma(fx, ux, mul(fy, uy)), t3);
+        t4 = fma(nrho, fma(fx, ux, mul(fy, nuy)), t4);
+        t5 = fma(nrh, fma(fx, uy, mul(fy, ux)), t5);
+        t6 = fma(nrh, fma(fy, ux2, mul(mul(k(2.0), fx), uxy)), t6);
+        t7 = fma(nrh, fma(fx, uy2, mul(mul(k(2.0), fy), uxy)), t7);
+        t8 = fma(nrho, fma(fx, mul(ux, uy2), mul(fy, mul(uy, ux2))), t8);
     }
-    const R g3 = c.s3_12 * t3;
-    const R g4 = sv4 * t4;
-    const R g5 = sv4 * t5;
-    const R h34p = R(3) * g3 + g4, h34m = R(3) * g3 - g4;
-    const R g6 = sq4 * t6 - R(0.5) * uy * h34p - R(2) * ux * g5;
-    const R g7 = sq4 * t7 - R(0.5) * ux * h34m - R(2) * uy * g5;
-    const R g8 = c.s8_4 * t8 - R(2) * g3 - R(0.5) * (uy2 * h34p + ux2 * h34m) - R(4) * uxy * g5 -
-                 R(2) * (uy * g6 + ux * g7);
+    // kernels g3..g8; hp, hm = (3 g3 +- g4) / 2
+    const L g3 = prod(bc<L>(c.s3_12), t3);
+    const L g4 = prod(sv4, t4);
+    const L g5 = prod(sv4, t5);
+    const L hp = fma(k(1.5), g3, mul(k(0.5), g4));
+    const L hm = fma(k(1.5), g3, mul(k(-0.5), g4));
+    const L g6 = fma(sq4, t6, fma(nuy, hp, mul(nux_2, g5)));
+    const L g7 = fma(sq4, t7, fma(nux, hm, mul(nuy_2, g5)));
+    // minus the bracket of g8: 2 g3 + uy^2 hp + ux^2 hm + 4 ux uy g5 + 2 uy g6 + 2 ux g7
+    L nb8 = mul(k(-2.0), g3);
+    nb8 = fma(mul(nuy, uy), hp, nb8);
+    nb8 = fma(mul(nux, ux), hm, nb8);
+    nb8 = fma(mul(k(-4.0), uxy), g5, nb8);
+    nb8 = fma(nuy_2, g6, nb8);
+    nb8 = fma(nux_2, g7, nb8);
+    const L g8 = fma(bc<L>(c.s8_4), t8, nb8);
     // Eq. 6 (g0 = g1 = g2 = 0)
-    const R ca = g4 - g3, cb = -g3 - g4, ce = R(2) * g3 + g8;
-    d[0] += R(-4) * (g3 - g8);
-    d[1] += ca + R(2) * (g7 - g8);
-    d[3] += ca - R(2) * (g7 + g8);
-    d[2] += cb + R(2) * (g6 - g8);
-    d[4] += cb - R(2) * (g6 + g8);
-    d[5] += ce + g5 - g6 - g7;
-    d[6] += ce - g5 - g6 + g7;
-    d[7] += ce + g5 + g6 + g7;
-    d[8] += ce - g5 + g6 - g7;
+    d[0] = fma(k(-4.0), sub(g3, g8), d[0]);
+    const L ca = sub(g4, g3), s34 = add(g3, g4), ce = fma(k(2.0), g3, g8);
+    d[1] = add(d[1], fma(k(2.0), sub(g7, g8), ca));
+    d[3] = add(d[3], fma(k(-2.0), add(g7, g8), ca));
+    d[2] = sub(d[2], fma(k(-2.0), sub(g6, g8), s34));
+    d[4] = sub(d[4], fma(k(2.0), add(g6, g8), s34));
+    const L e5 = add(ce, g5), e6 = sub(ce, g5), gp = add(g6, g7), gm = sub(g6, g7);
+    d[5] = add(d[5], sub(e5, gp));
+    d[7] = add(d[7], add(e5, gp));
+    d[6] = add(d[6], sub(e6, gm));
+    d[8] = add(d[8], add(e6, gm));
     if (MODE == MODE_PERIODIC) {
-        // source S = T^-1 S^ (Eq. 9-10)
-        const R fx = c.fx, fy = c.fy;
-        R m[9];
-        m[0] = R(0);
-        m[1] = rho * fx;
-        m[2] = rho * fy;
-        m[3] = R(2) * rho * (ux * fx + uy * fy);
-        m[4] = R(2) * rho * (ux * fx - uy * fy);
-        m[5] = rho * (ux * fy + uy * fx);
-        m[6] = rho * (fy * ux2 + R(2) * fx * uxy);
-        m[7] = rho * (fx * uy2 + R(2) * fy * uxy);
-        m[8] = R(2) * rho * uxy * (fx * uy + fy * ux);
-        R S[9];
-        tinv_apply(m, S);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) d[i] += S[i];
+        // source S = T^-1 S^ (Eq. 9-10), T^-1 in closed form as tinv_apply
+        const L fx = bc<L>(c.fx), fy = bc<L>(c.fy), two = k(2.0), qt = k(0.25);
+        const L m1 = prod(rho, fx);
+        const L m2 = prod(rho, fy);
+        const L m3 = mul(two, prod(rho, fma(ux, fx, mul(uy, fy))));
+        const L m4 = mul(two, prod(rho, fma(ux, fx, mul(nuy, fy))));
+        const L m5 = prod(rho, fma(ux, fy, mul(uy, fx)));
+        const L m6 = prod(rho, fma(fy, ux2, mul(mul(two, fx), uxy)));
+        const L m7 = prod(rho, fma(fx, uy2, mul(mul(two, fy), uxy)));
+        const L m8 = mul(two, prod(rho, mul(uxy, fma(fx, uy, mul(fy, ux)))));
+        const L cm = fma(k(-2.0), m8, m3);
+        const L b4 = add(cm, m4), e4 = sub(cm, m4);
+        const L a17 = mul(two, sub(m1, m7)), a26 = mul(two, sub(m2, m6));
+        const L p56 = add(m5, m6), n56 = sub(m6, m5);
+        const L p78 = add(m7, m8), n78 = sub(m8, m7);
+        d[0] = add(d[0], sub(m8, m3));  // S_0 = m0 - m3 + m8 with m0 = 0
+        d[1] = add(d[1], mul(qt, add(b4, a17)));
+        d[3] = add(d[3], mul(qt, sub(b4, a17)));
+        d[2] = add(d[2], mul(qt, add(e4, a26)));
+        d[4] = add(d[4], mul(qt, sub(e4, a26)));
+        d[5] = add(d[5], mul(qt, add(p56, p78)));
+        d[6] = add(d[6], mul(qt, add(n56, n78)));
+        d[7] = add(d[7], mul(qt, sub(n78, n56)));
+        d[8] = add(d[8], mul(qt, sub(p78, p56)));
     }
 }
 

@@ -188,8 +188,8 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) sweep_kernel(const S
 #pragma unroll
         for (int k = 0; k < V; ++k) {
             f[2][k] = v4[k];
-            f[5][k] = c.r * v7[k] + c.rc * s8[k];
-            f[6][k] = c.r * v8[k] + c.rc * s7[k];
+            f[5][k] = ln::fma(c.r, v7[k], ln::mul(c.rc, s8[k]));
+            f[6][k] = ln::fma(c.r, v8[k], ln::mul(c.rc, s7[k]));
         }
     } else {
         const T* rd = row - a.pitch;
@@ -220,8 +220,8 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) sweep_kernel(const S
 #pragma unroll
         for (int k = 0; k < V; ++k) {
             f[4][k] = v2[k];
-            f[7][k] = c.r * v5[k] + c.rc * s6[k];
-            f[8][k] = c.r * v6[k] + c.rc * s5[k];
+            f[7][k] = ln::fma(c.r, v5[k], ln::mul(c.rc, s6[k]));
+            f[8][k] = ln::fma(c.r, v6[k], ln::mul(c.rc, s5[k]));
         }
     } else {
         const T* ru = row + a.pitch;
@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) sweep_kernel(const S
         R d[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) d[i] = f[i][k];
-        const R ref = (MODE == MODE_PRESSURE) ? c.ref0 + c.slope * R(x0 + k) : c.ref0;
+        const R ref = (MODE == MODE_PRESSURE) ? ln::fma(c.slope, R(x0 + k), c.ref0) : c.ref0;
         if (centre_kn && (y == a.yc0 || y == a.yc1) && x0 + k < a.nx) {
             R dr = d[0];
 #pragma unroll

@@ -116,17 +116,23 @@ template <> struct VecT<__nv_bfloat16, 2> { using type = unsigned int; };
 template <class T> struct Pair16 {
     static constexpr bool ok = false;
 };
+// FP16 applies the field scale to both values with one packed multiply.
 template <> struct Pair16<__half> {
     static constexpr bool ok = true;
     using P = __half2;
-    static __device__ __forceinline__ float2 dec(P p) { return __half22float2(p); }
-    static __device__ __forceinline__ P enc(float a, float b) { return __floats2half2_rn(a, b); }
+    static __device__ __forceinline__ float2 dec(P p, float isc) {
+        return ln::mul(__half22float2(p), ln::bc<float2>(isc));
+    }
+    static __device__ __forceinline__ P enc(float2 v, float sc) {
+        const float2 s = ln::mul(v, ln::bc<float2>(sc));
+        return __floats2half2_rn(s.x, s.y);
+    }
 };
 template <> struct Pair16<__nv_bfloat16> {
     static constexpr bool ok = true;
     using P = __nv_bfloat162;
-    static __device__ __forceinline__ float2 dec(P p) { return __bfloat1622float2(p); }
-    static __device__ __forceinline__ P enc(float a, float b) { return __floats2bfloat162_rn(a, b); }
+    static __device__ __forceinline__ float2 dec(P p, float) { return __bfloat1622float2(p); }
+    static __device__ __forceinline__ P enc(float2 v, float) { return __floats2bfloat162_rn(v.x, v.y); }
 };
 
 template <class T, int NC, int V, int S> struct Geometry {
@@ -203,9 +209,9 @@ __device__ __forceinline__ void tile_update(const SweepArgs& a, const KC<typenam
             // two 16-bit values per conversion (exact, as the scalar one)
 #pragma unroll
             for (int k = 0; k < V; k += 2) {
-                const float2 q = Pair16<T>::dec(reinterpret_cast<const typename Pair16<T>::P*>(e)[k / 2]);
-                w[i][k + 1] = Codec<T>::unscale(q.x, c.isc);
-                w[i][k + 2] = Codec<T>::unscale(q.y, c.isc);
+                const float2 q = Pair16<T>::dec(reinterpret_cast<const typename Pair16<T>::P*>(e)[k / 2], c.isc);
+                w[i][k + 1] = q.x;
+                w[i][k + 2] = q.y;
             }
         } else {
 #pragma unroll
@@ -224,8 +230,8 @@ __device__ __forceinline__ void tile_update(const SweepArgs& a, const KC<typenam
         f[3][k] = at(3, k + 1);
         if (rt & ROW_BOTTOM) {
             f[2][k] = at(2, k);
-            f[5][k] = c.r * at(5, k) + c.rc * (at(6, k - 1) + (kShift ? c.shd : R(0)));
-            f[6][k] = c.r * at(6, k) + c.rc * (at(5, k + 1) - (kShift ? c.shd : R(0)));
+            f[5][k] = ln::fma(c.r, at(5, k), ln::mul(c.rc, at(6, k - 1) + (kShift ? c.shd : R(0))));
+            f[6][k] = ln::fma(c.r, at(6, k), ln::mul(c.rc, at(5, k + 1) - (kShift ? c.shd : R(0))));
         } else {
             f[2][k] = at(2, k);
             f[5][k] = at(5, k - 1);
@@ -237,8 +243,8 @@ __device__ __forceinline__ void tile_update(const SweepArgs& a, const KC<typenam
         }
         if (rt & ROW_TOP) {
             f[4][k] = at(4, k);
-            f[7][k] = c.r * at(7, k) + c.rc * (at(8, k + 1) - (kShift ? c.shd : R(0)));
-            f[8][k] = c.r * at(8, k) + c.rc * (at(7, k - 1) + (kShift ? c.shd : R(0)));
+            f[7][k] = ln::fma(c.r, at(7, k), ln::mul(c.rc, at(8, k + 1) - (kShift ? c.shd : R(0))));
+            f[8][k] = ln::fma(c.r, at(8, k), ln::mul(c.rc, at(7, k - 1) + (kShift ? c.shd : R(0))));
         } else {
             f[4][k] = at(4, k);
             f[7][k] = at(7, k + 1);
@@ -280,15 +286,40 @@ __device__ __forceinline__ void tile_update(const SweepArgs& a, const KC<typenam
                     for (int i = 0; i < 9; ++i) f[i][k] = t[i];
         }
     }
+    // The 16-bit sweeps are bound by instruction issue as much as by HBM, so
+    // they collide nodes k and k + 1 together in packed FP32 (bit for bit the
+    // scalar collision, with about a third fewer instructions per node).  The
+    // FP32 sweep is bound by HBM alone: there the packed form finished its
+    // arithmetic sooner but moved the bytes less evenly, and back-to-back
+    // steps got slower, so it collides one node per lane.
+    if constexpr (Pair16<T>::ok && V % 2 == 0) {
 #pragma unroll
-    for (int k = 0; k < V; ++k) {
-        R d[9];
+        for (int k = 0; k < V; k += 2) {
+            float2 d[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) d[i] = f[i][k];
-        const R ref = (MODE == MODE_PRESSURE) ? c.ref0 + c.slope * R(x0 + k) : c.ref0;
-        collide<R, MODE>(d, ref, c);
+            for (int i = 0; i < 9; ++i) d[i] = make_float2(f[i][k], f[i][k + 1]);
+            const float2 ref = (MODE == MODE_PRESSURE)
+                                   ? ln::fma(ln::bc<float2>(c.slope), make_float2(float(x0 + k), float(x0 + k + 1)),
+                                             ln::bc<float2>(c.ref0))
+                                   : ln::bc<float2>(c.ref0);
+            collide<R, MODE, float2>(d, ref, c);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) f[i][k] = d[i];
+            for (int i = 0; i < 9; ++i) {
+                f[i][k] = d[i].x;
+                f[i][k + 1] = d[i].y;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            R d[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) d[i] = f[i][k];
+            const R ref = (MODE == MODE_PRESSURE) ? ln::fma(c.slope, R(x0 + k), c.ref0) : c.ref0;
+            collide<R, MODE>(d, ref, c);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) f[i][k] = d[i];
+        }
     }
     const long long P = dst_plane;
     T* orow = dst + (long long)(y & dst_rmask) * a.pitch + a.xoff;
@@ -302,7 +333,7 @@ __device__ __forceinline__ void tile_update(const SweepArgs& a, const KC<typenam
 #pragma unroll
                 for (int k = 0; k < V; k += 2)
                     reinterpret_cast<typename Pair16<T>::P*>(e)[k / 2] =
-                        Pair16<T>::enc(Codec<T>::prescale(f[i][k], c.sc), Codec<T>::prescale(f[i][k + 1], c.sc));
+                        Pair16<T>::enc(make_float2(f[i][k], f[i][k + 1]), c.sc);
             } else {
 #pragma unroll
                 for (int k = 0; k < V; ++k) e[k] = Codec<T>::enc(f[i][k], c.sc);
