@@ -426,8 +426,8 @@ def errors_vs_oracle(clb, variants, ref, steps):
 
 
 # tile shapes of the TMA-staged sweep: (consumer threads, nodes per thread, stages)
-TMA_SHAPES = [(128, 4, 4), (256, 4, 3), (256, 2, 4), (256, 2, 6), (256, 1, 8), (256, 4, 4), (512, 1, 4),
-              (128, 2, 8), (512, 1, 6), (512, 1, 4), (384, 1, 4), (384, 1, 6), (512, 2, 3)]
+TMA_SHAPES = [(128, 4, 4), (256, 4, 3), (256, 2, 4), (256, 2, 6), (256, 1, 8), (256, 4, 4), (224, 4, 3),
+              (128, 2, 8), (224, 4, 4), (512, 1, 4), (384, 1, 4), (384, 1, 6), (512, 2, 3)]
 
 
 # tile shapes of the two-step sweep (pipelines 15..19)

@@ -74,9 +74,15 @@ struct SweepArgs {
     int withhold_tile;        // testing: TMA tile whose inputs are never sent (-1: none)
     KC<float> kf;             // the constants above, derived, in FP32
     KC<double> kd;            // ... and in FP64
+    // kf in the units of the stored values: every density-like constant times
+    // the storage scale (a power of two, so exactly), sc = isc = 1.  The
+    // TMA-staged sweeps collide the stored 16-bit values without unscaling
+    // them; the collision is homogeneous in the densities, so the results are
+    // the scaled results bit for bit.
+    KC<float> ks;
 };
 
-// Fill a.kf and a.kd from the double fields of a.
+// Fill a.kf, a.kd and a.ks from the double fields of a.
 void derive_constants(SweepArgs& a);
 
 // s_v (Eq. 18) and s_q (Eq. 21) at a Knudsen number, N = ny.

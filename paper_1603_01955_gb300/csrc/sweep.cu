@@ -377,6 +377,21 @@ template <typename R> static void fill(KC<R>& c, const SweepArgs& a) {
 void derive_constants(SweepArgs& a) {
     fill(a.kf, a);
     fill(a.kd, a);
+    // densities scale, 1/densities scale inversely, rates and velocities do not
+    KC<float>& k = a.ks;
+    k = a.kf;
+    const float s = a.kf.sc;
+    k.A *= s;
+    k.B *= s;
+    k.CA *= s;
+    k.A316 /= s;
+    k.ref0 *= s;
+    k.slope *= s;
+    k.sha *= s;
+    k.shd *= s;
+    k.drho_in *= s;
+    k.drho_out *= s;
+    k.sc = k.isc = 1.0f;
 }
 
 bool sweep_supported(int storage, int vec) {

@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(NC + 64, MB) sweep_pair_kernel(const SweepArgs
     __shared__ int pub_item[Q];  // work item of each publication slot
     __shared__ int published;    // tiles counted by the publisher
     __shared__ int abort_flag;
-    const KC<R>& c = kc<R>(a);
+    const KC<R>& c = a.ks;  // constants in the units of the stored values
     T* ring = static_cast<T*>(p.ring);
     // The source field of a work item is built from scalar selects: with
     // whole-struct selects or copies of two such fields (`level ? fR : fA`)

@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(NC + 32, MB) sweep_tma_kernel(const SweepArgs 
     __shared__ int abort_flag;
     const T* __restrict__ fin = static_cast<const T*>(a.fin);
     T* __restrict__ fout = static_cast<T*>(a.fout);
-    const KC<R>& c = kc<R>(a);
+    const KC<R>& c = a.ks;  // constants in the units of the stored values
     const Field<T> src{fin, a.plane, -1};
 
     if (threadIdx.x == 0) {
@@ -149,7 +149,7 @@ cudaError_t launch_tma_one(const SweepArgs& a, cudaStream_t st, unsigned* status
 // stages, blocks per SM the registers are sized for) from this table.
 #define CLB_TMA_VARIANTS(X)                                                                             \
     X(0, 128, 4, 4, 3) X(1, 256, 4, 3, 2) X(2, 256, 2, 4, 2) X(3, 256, 2, 6, 2) X(4, 256, 1, 8, 2)      \
-    X(5, 256, 4, 4, 2) X(6, 512, 1, 4, 1) X(7, 128, 2, 8, 3) X(8, 512, 1, 6, 1) X(9, 512, 1, 4, 2)      \
+    X(5, 256, 4, 4, 2) X(6, 224, 4, 3, 2) X(7, 128, 2, 8, 3) X(8, 224, 4, 4, 2) X(9, 512, 1, 4, 2)      \
     X(10, 384, 1, 4, 2) X(11, 384, 1, 6, 2) X(12, 512, 2, 3, 1)
 
 int tma_variant_count() { return 13; }

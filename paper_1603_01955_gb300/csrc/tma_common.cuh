@@ -116,23 +116,36 @@ template <> struct VecT<__nv_bfloat16, 2> { using type = unsigned int; };
 template <class T> struct Pair16 {
     static constexpr bool ok = false;
 };
-// FP16 applies the field scale to both values with one packed multiply.
 template <> struct Pair16<__half> {
     static constexpr bool ok = true;
     using P = __half2;
-    static __device__ __forceinline__ float2 dec(P p, float isc) {
-        return ln::mul(__half22float2(p), ln::bc<float2>(isc));
-    }
-    static __device__ __forceinline__ P enc(float2 v, float sc) {
-        const float2 s = ln::mul(v, ln::bc<float2>(sc));
-        return __floats2half2_rn(s.x, s.y);
-    }
+    static __device__ __forceinline__ float2 dec(P p) { return __half22float2(p); }
+    static __device__ __forceinline__ P enc(float2 v) { return __floats2half2_rn(v.x, v.y); }
 };
 template <> struct Pair16<__nv_bfloat16> {
     static constexpr bool ok = true;
     using P = __nv_bfloat162;
-    static __device__ __forceinline__ float2 dec(P p, float) { return __bfloat1622float2(p); }
-    static __device__ __forceinline__ P enc(float2 v, float) { return __floats2bfloat162_rn(v.x, v.y); }
+    static __device__ __forceinline__ float2 dec(P p) { return __bfloat1622float2(p); }
+    static __device__ __forceinline__ P enc(float2 v) { return __floats2bfloat162_rn(v.x, v.y); }
+};
+
+// A stored value as it is, in FP32 (no storage scale: the sweeps that use
+// this collide in the units of the stored values, with SweepArgs::ks).
+template <class T> struct Raw {
+    static __device__ __forceinline__ float dec(T v) { return float(v); }
+    static __device__ __forceinline__ T enc(float v) { return T(v); }
+};
+template <> struct Raw<float> {
+    static __device__ __forceinline__ float dec(float v) { return v; }
+    static __device__ __forceinline__ float enc(float v) { return v; }
+};
+template <> struct Raw<__half> {
+    static __device__ __forceinline__ float dec(__half v) { return __half2float(v); }
+    static __device__ __forceinline__ __half enc(float v) { return __float2half_rn(v); }
+};
+template <> struct Raw<__nv_bfloat16> {
+    static __device__ __forceinline__ float dec(__nv_bfloat16 v) { return __bfloat162float(v); }
+    static __device__ __forceinline__ __nv_bfloat16 enc(float v) { return __float2bfloat16_rn(v); }
 };
 
 template <class T, int NC, int V, int S> struct Geometry {
@@ -185,6 +198,8 @@ __device__ __forceinline__ void load_tile(const SweepArgs& a, const Field<T> f, 
 // storage, releases the stage on `empty`, rebuilds pressure columns from the
 // field `src` (Sec. 3.2), collides (Eq. 4-13, 18, 21) and stores to the
 // field `dst` (periodic channels also write the halo columns -1 and nx).
+// c: the constants in the units of the stored values (SweepArgs::ks), so
+// 16-bit values are converted without a scale multiply.
 // kCG: `src` was written earlier in the same launch.
 template <class T, int MODE, int V, int SEG, bool kCG>
 __device__ __forceinline__ void tile_update(const SweepArgs& a, const KC<typename Codec<T>::R>& c, const T* stage,
@@ -209,16 +224,16 @@ __device__ __forceinline__ void tile_update(const SweepArgs& a, const KC<typenam
             // two 16-bit values per conversion (exact, as the scalar one)
 #pragma unroll
             for (int k = 0; k < V; k += 2) {
-                const float2 q = Pair16<T>::dec(reinterpret_cast<const typename Pair16<T>::P*>(e)[k / 2], c.isc);
+                const float2 q = Pair16<T>::dec(reinterpret_cast<const typename Pair16<T>::P*>(e)[k / 2]);
                 w[i][k + 1] = q.x;
                 w[i][k + 2] = q.y;
             }
         } else {
 #pragma unroll
-            for (int k = 0; k < V; ++k) w[i][k + 1] = Codec<T>::dec(e[k], c.isc);
+            for (int k = 0; k < V; ++k) w[i][k + 1] = Raw<T>::dec(e[k]);
         }
-        w[i][0] = (i == 1 || i >= 5) ? Codec<T>::dec(p[-1], c.isc) : R(0);
-        w[i][V + 1] = (i == 3 || i >= 5) ? Codec<T>::dec(p[V], c.isc) : R(0);
+        w[i][0] = (i == 1 || i >= 5) ? Raw<T>::dec(p[-1]) : R(0);
+        w[i][V + 1] = (i == 3 || i >= 5) ? Raw<T>::dec(p[V]) : R(0);
     }
     // element of slot i at column x0 + k (k may be -1 .. V)
     auto at = [&](int i, int k) -> R { return w[i][k + 1]; };
@@ -333,10 +348,10 @@ __device__ __forceinline__ void tile_update(const SweepArgs& a, const KC<typenam
 #pragma unroll
                 for (int k = 0; k < V; k += 2)
                     reinterpret_cast<typename Pair16<T>::P*>(e)[k / 2] =
-                        Pair16<T>::enc(make_float2(f[i][k], f[i][k + 1]), c.sc);
+                        Pair16<T>::enc(make_float2(f[i][k], f[i][k + 1]));
             } else {
 #pragma unroll
-                for (int k = 0; k < V; ++k) e[k] = Codec<T>::enc(f[i][k], c.sc);
+                for (int k = 0; k < V; ++k) e[k] = Raw<T>::enc(f[i][k]);
             }
             *reinterpret_cast<VT*>(orow + i * P + x0) = v;
         }
@@ -345,21 +360,21 @@ __device__ __forceinline__ void tile_update(const SweepArgs& a, const KC<typenam
         for (int k = 0; k < V; ++k)
             if (x0 + k < a.nx)
 #pragma unroll
-                for (int i = 0; i < 9; ++i) orow[i * P + x0 + k] = Codec<T>::enc(f[i][k], c.sc);
+                for (int i = 0; i < 9; ++i) orow[i * P + x0 + k] = Raw<T>::enc(f[i][k]);
     }
     if (MODE == MODE_PERIODIC) {
         // column 0 is mirrored into the halo column nx, column nx - 1 into -1
 #pragma unroll
         for (int k = 0; k < V; ++k) {
             if (k == kfirst) {
-                orow[3 * P + a.nx] = Codec<T>::enc(f[3][k], c.sc);
-                orow[6 * P + a.nx] = Codec<T>::enc(f[6][k], c.sc);
-                orow[7 * P + a.nx] = Codec<T>::enc(f[7][k], c.sc);
+                orow[3 * P + a.nx] = Raw<T>::enc(f[3][k]);
+                orow[6 * P + a.nx] = Raw<T>::enc(f[6][k]);
+                orow[7 * P + a.nx] = Raw<T>::enc(f[7][k]);
             }
             if (k == klast) {
-                orow[1 * P - 1] = Codec<T>::enc(f[1][k], c.sc);
-                orow[5 * P - 1] = Codec<T>::enc(f[5][k], c.sc);
-                orow[8 * P - 1] = Codec<T>::enc(f[8][k], c.sc);
+                orow[1 * P - 1] = Raw<T>::enc(f[1][k]);
+                orow[5 * P - 1] = Raw<T>::enc(f[5][k]);
+                orow[8 * P - 1] = Raw<T>::enc(f[8][k]);
             }
         }
     }
