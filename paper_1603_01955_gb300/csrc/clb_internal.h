@@ -10,15 +10,12 @@ namespace clb {
 
 enum : int { MODE_PERIODIC = 0, MODE_PRESSURE = 1 };
 
-// row_type bits: the first / last row touches the bottom / top wall.
+// Row kinds: the first / last row touches the bottom / top wall.  The kernels
+// compute them from the row index (row_kind); the end columns' roles
+// (pressure inlet / outlet, or the columns mirrored into the periodic halo
+// columns -1 and nx so that the next sweep needs no wrap-around) follow from
+// x = 0 and x = nx - 1 in the same way, so no node-type mask is stored.
 enum : uint8_t { ROW_BOTTOM = 1, ROW_TOP = 2 };
-// col_type bits: pressure inlet / outlet column (rebuilt before the collision),
-// and, for periodic x, the columns whose outgoing populations are mirrored into
-// the halo columns -1 and nx so that the next sweep needs no wrap-around.
-enum : uint8_t { COL_INLET = 1, COL_OUTLET = 2, COL_HALO_RIGHT = 4, COL_HALO_LEFT = 8 };
-
-// The row_type bits of row y, from the index alone (the same bits the row
-// mask holds); kernels that walk rows compute them instead of loading them.
 __host__ __device__ __forceinline__ int row_kind(int y, int ny) {
     return (y == 0 ? ROW_BOTTOM : 0) | (y == ny - 1 ? ROW_TOP : 0);
 }
@@ -47,8 +44,6 @@ struct SweepArgs {
     int pitch;                // elements per stored row
     int xoff;                 // element index of column 0 in a row (column -1 is xoff-1)
     long long plane;          // elements per direction plane (= ny * pitch)
-    const uint8_t* row_type;  // [ny]
-    const uint8_t* col_type;  // [>= nx + 16], zero past nx-1
     // collision (Eq. 7, 14, 18, 21)
     double s3, s8;
     double sv, sq;            // constant rates (body-force channel)

@@ -75,9 +75,6 @@ struct clb_sim {
     size_t buf_bytes = 0;
     void* buf[2] = {nullptr, nullptr};
     int cur = 0;            // buffer holding the last completed step
-    uint8_t* row_type = nullptr;
-    uint8_t* col_type = nullptr;
-    size_t col_bytes = 0;
     double* obs = nullptr;  // device scratch of the observable reductions
     unsigned* status = nullptr;  // error bits of bounded device waits
     int pipeline = 1;       // 1 direct loads, 2..14 TMA-staged variants, 15.. two-step variants
@@ -329,8 +326,6 @@ SweepArgs make_args(const clb_sim* s) {
     a.pitch = s->pitch;
     a.xoff = s->xoff;
     a.plane = s->plane;
-    a.row_type = s->row_type;
-    a.col_type = s->col_type;
     a.s3 = s->s3;
     a.s8 = s->s8;
     a.sv = s->sv;
@@ -433,8 +428,6 @@ clb_status clb_destroy(clb_sim* s) {
     if (s->stream) cudaStreamSynchronize(s->stream);
     s->dfree(s->buf[0]);
     s->dfree(s->buf[1]);
-    s->dfree(s->row_type);
-    s->dfree(s->col_type);
     s->dfree(s->obs);
     s->dfree(s->status);
     s->dfree(s->rc);
@@ -562,7 +555,6 @@ clb_status clb_create(int nx, int ny, double kn, double a, double r, clb_drive d
     s->plane = (long long)ny * s->pitch;
     s->buf_bytes = (size_t)9 * s->plane * s->elem;
     s->L = obs_layout(nx, ny);
-    s->col_bytes = (size_t)((nx + 16 + 15) / 16) * 16;
 
     if (o.stream) {
         s->stream = static_cast<cudaStream_t>(o.stream);
@@ -577,13 +569,11 @@ clb_status clb_create(int nx, int ny, double kn, double a, double r, clb_drive d
 
     s->buf[0] = s->dalloc(s->buf_bytes);
     s->buf[1] = s->dalloc(s->buf_bytes);
-    s->row_type = static_cast<uint8_t*>(s->dalloc(ny));
-    s->col_type = static_cast<uint8_t*>(s->dalloc(s->col_bytes));
     s->obs = static_cast<double*>(s->dalloc(s->L.total * sizeof(double)));
     s->status = static_cast<unsigned*>(s->dalloc(sizeof(unsigned)));
     s->rc_stride = ((nx + 16 + 31) / 32) * 32;
     s->rc = s->dalloc((size_t)4 * s->rc_stride * (o.storage == CLB_FP64 ? 8 : 4));
-    if (!s->buf[0] || !s->buf[1] || !s->row_type || !s->col_type || !s->obs || !s->status || !s->rc) {
+    if (!s->buf[0] || !s->buf[1] || !s->obs || !s->status || !s->rc) {
         clb_destroy(s);
         return fail(CLB_ENOMEM, "clb_create: device allocation of %zu bytes failed", 2 * s->buf_bytes);
     }
@@ -609,23 +599,10 @@ clb_status clb_create(int nx, int ny, double kn, double a, double r, clb_drive d
         p.epoch = 0;
     }
 
-    // node-type masks (separable: row type x column type)
-    std::vector<uint8_t> rt(ny, 0), ct(s->col_bytes, 0);
-    rt[0] |= ROW_BOTTOM;
-    rt[ny - 1] |= ROW_TOP;
-    if (drive == CLB_DRIVE_PRESSURE) {
-        ct[0] |= COL_INLET;
-        ct[nx - 1] |= COL_OUTLET;
-    } else {
-        ct[0] |= COL_HALO_RIGHT;
-        ct[nx - 1] |= COL_HALO_LEFT;
-    }
     clb_status st = CLB_OK;
     auto chk = [&](cudaError_t e, const char* what) {
         if (e != cudaSuccess && st == CLB_OK) st = fail(CLB_ECUDA, "clb_create: %s: %s", what, cudaGetErrorString(e));
     };
-    chk(cudaMemcpyAsync(s->row_type, rt.data(), ny, cudaMemcpyHostToDevice, s->stream), "row mask");
-    chk(cudaMemcpyAsync(s->col_type, ct.data(), s->col_bytes, cudaMemcpyHostToDevice, s->stream), "column mask");
     chk(cudaMemsetAsync(s->buf[0], 0, s->buf_bytes, s->stream), "memset");
     chk(cudaMemsetAsync(s->buf[1], 0, s->buf_bytes, s->stream), "memset");
     chk(cudaMemsetAsync(s->obs, 0, s->L.total * sizeof(double), s->stream), "memset");

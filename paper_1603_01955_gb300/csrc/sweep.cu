@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) sweep_kernel(const S
     const KC<R>& c = kc<R>(a);
     const long long P = a.plane;
     const T* row = fin + (long long)y * a.pitch + a.xoff;  // plane 0, row y, column 0
-    const int rt = a.row_type[y];
+    const int rt = row_kind(y, a.ny);
 
     R f[9][V];
     // rest population and the two that move along x only (Eq. 5)
@@ -238,19 +238,13 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) sweep_kernel(const S
     }
     if (!live || x0 >= a.nx) return;  // nothing of this thread's own to store
 
-    // node-type mask of this thread's columns: at most one inlet and one
-    // outlet node, rebuilt here (Sec. 3.2) before the collision loop
-    uint8_t ct[V];
-    int kin = -1, kout = -1;
-#pragma unroll
-    for (int k = 0; k < V; ++k) {
-        ct[k] = a.col_type[x0 + k];
-        if (MODE == MODE_PRESSURE) {
-            if (ct[k] & COL_INLET) kin = k;
-            if (ct[k] & COL_OUTLET) kout = k;
-        }
-    }
+    // the thread's node in the first and in the last column, if any: the
+    // pressure inlet and outlet, rebuilt here (Sec. 3.2) before the collision
+    // loop, or the columns mirrored into the periodic halo
+    const int kfirst = x0 == 0 ? 0 : -1;
+    const int klast = a.nx - 1 - x0 < V ? a.nx - 1 - x0 : -1;
     if (MODE == MODE_PRESSURE) {
+        const int kin = kfirst, kout = klast;
         if (kin >= 0) {
             R t[9];
             rebuild_column<T, R>(a, c, Field<T>{fin, a.plane, -1}, x0 + kin, y, true, t);
@@ -320,12 +314,12 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) sweep_kernel(const S
         // (populations moving in -x), column nx-1 -> halo column -1 (moving in +x)
 #pragma unroll
         for (int k = 0; k < V; ++k) {
-            if (ct[k] & COL_HALO_RIGHT) {
+            if (k == kfirst) {
                 orow[3 * P + a.nx] = Codec<T>::enc(f[3][k], c.sc);
                 orow[6 * P + a.nx] = Codec<T>::enc(f[6][k], c.sc);
                 orow[7 * P + a.nx] = Codec<T>::enc(f[7][k], c.sc);
             }
-            if (ct[k] & COL_HALO_LEFT) {
+            if (k == klast) {
                 orow[1 * P - 1] = Codec<T>::enc(f[1][k], c.sc);
                 orow[5 * P - 1] = Codec<T>::enc(f[5][k], c.sc);
                 orow[8 * P - 1] = Codec<T>::enc(f[8][k], c.sc);
