@@ -173,6 +173,12 @@ __device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) {
         : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
     return r;
 }
+// -a: free as an operand of a scalar fused multiply-add; one exact packed
+// multiply for float2
+__device__ __forceinline__ float neg(float a) { return -a; }
+__device__ __forceinline__ double neg(double a) { return -a; }
+__device__ __forceinline__ float2 neg(float2 a) { return mul(a, make_float2(-1.0f, -1.0f)); }
+template <class L> __device__ __forceinline__ L neg(L a) { return -a; }
 template <class L> __device__ __forceinline__ L add(L a, L b) { return a + b; }
 template <class L> __device__ __forceinline__ L sub(L a, L b) { return a - b; }
 template <class L> __device__ __forceinline__ L mul(L a, L b) { return a * b; }
@@ -220,9 +226,34 @@ __device__ __forceinline__ void collide(L (&d)[9], L ref, const KC<R>& c, const 
     const L drho = add(add(add(d[0], s13), s24), kxxyy);
     const L jx = add(sub(d[1], d[3]), kxyy);
     const L jy = add(sub(d[2], d[4]), kxxy);
-    // Eq. 12-13
+    // Eq. 12-13 and the relaxation rates: tau = A/q, q = rho + B;
+    // s_v/4 = (q/4) / hv, hv = q/2 + A (Eq. 18);
+    // s_q/4 = (q/4) / hq, hq = q (1/2 + 3q/(16A)) + (pi B2/4) A (Eq. 21)
     const L rho = add(ref, drho);
-    const L irho = rcp(rho);
+    L irho, sv4, sq4;
+    if (MODE == MODE_PRESSURE) {
+        const L q = add(rho_kn ? *rho_kn : rho, bc<L>(c.B));
+        const L q4 = mul(q, k(0.25));
+        const L hv = fma(q, k(0.5), bc<L>(c.A));
+        const L hq = fma(q, fma(bc<L>(c.A316), q, k(0.5)), bc<L>(c.CA));
+        if constexpr (std::is_same<L, double>::value) {
+            // FP64 pipe bound: one reciprocal, 1 / (rho hv hq), for all three
+            const L p = mul(hv, hq);
+            const L inv = rcp(mul(rho, p));
+            const L ri = mul(rho, inv);
+            irho = mul(p, inv);
+            sv4 = mul(mul(q4, hq), ri);
+            sq4 = mul(mul(q4, hv), ri);
+        } else {
+            irho = rcp(rho);
+            sv4 = mul(q4, rcp(hv));
+            sq4 = mul(q4, rcp(hq));
+        }
+    } else {
+        irho = rcp(rho);
+        sv4 = bc<L>(c.sv_4);
+        sq4 = bc<L>(c.sq_4);
+    }
     L ux, uy;
     if (MODE == MODE_PERIODIC) {
         ux = fma(jx, irho, bc<L>(c.hfx));
@@ -231,22 +262,10 @@ __device__ __forceinline__ void collide(L (&d)[9], L ref, const KC<R>& c, const 
         ux = mul(jx, irho);
         uy = mul(jy, irho);
     }
-    // relaxation rates: tau = A/q, q = rho + B; s_v/4 = (q/4) / (q/2 + A)
-    // (Eq. 18); s_q/4 = (q/4) / (q (1/2 + 3q/(16A)) + (pi B2/4) A) (Eq. 21)
-    L sv4, sq4;
-    if (MODE == MODE_PRESSURE) {
-        const L q = add(rho_kn ? *rho_kn : rho, bc<L>(c.B));
-        const L q4 = mul(q, k(0.25));
-        sv4 = mul(q4, rcp(fma(q, k(0.5), bc<L>(c.A))));
-        sq4 = mul(q4, rcp(fma(q, fma(bc<L>(c.A316), q, k(0.5)), bc<L>(c.CA))));
-    } else {
-        sv4 = bc<L>(c.sv_4);
-        sq4 = bc<L>(c.sq_4);
-    }
     const L ux2 = mul(ux, ux), uy2 = mul(uy, uy), uxy = mul(ux, uy);
-    const L nux = mul(k(-1.0), ux), nuy = mul(k(-1.0), uy);
+    const L nux = neg(ux), nuy = neg(uy);
     const L ux_2 = mul(k(2.0), ux), uy_2 = mul(k(2.0), uy);
-    const L nux_2 = mul(k(-2.0), ux), nuy_2 = mul(k(-2.0), uy);
+    const L nux_2 = neg(ux_2), nuy_2 = neg(uy_2);
     const L kxxf = fma(k(1.0 / 3.0), ref, kxx);  // full k'_xx
     const L kyyf = fma(k(1.0 / 3.0), ref, kyy);  // full k'_yy
     // Eq. 7, in cascade order.  t5u = rho ux uy - k'_xy is the xy brace
@@ -263,7 +282,7 @@ __device__ __forceinline__ void collide(L (&d)[9], L ref, const KC<R>& c, const 
                fma(ux2, kyyf, fma(uy2, kxxf, kxxyy)));
     if (MODE == MODE_PERIODIC) {
         const L fx = bc<L>(c.fx), fy = bc<L>(c.fy);
-        const L nrho = sub(k(0.0), rho), nrh = mul(k(0.5), nrho);
+        const L nrho = neg(rho), nrh = mul(k(0.5), nrho);
         t3 = fma(nrho, fma(fx, ux, mul(fy, uy)), t3);
         t4 = fma(nrho, fma(fx, ux, mul(fy, nuy)), t4);
         t5 = fma(nrh, fma(fx, uy, mul(fy, ux)), t5);
@@ -281,8 +300,8 @@ __device__ __forceinline__ void collide(L (&d)[9], L ref, const KC<R>& c, const 
     const L g7 = fma(sq4, t7, fma(nux, hm, mul(nuy_2, g5)));
     // minus the bracket of g8: 2 g3 + uy^2 hp + ux^2 hm + 4 ux uy g5 + 2 uy g6 + 2 ux g7
     L nb8 = mul(k(-2.0), g3);
-    nb8 = fma(mul(nuy, uy), hp, nb8);
-    nb8 = fma(mul(nux, ux), hm, nb8);
+    nb8 = fma(neg(uy2), hp, nb8);
+    nb8 = fma(neg(ux2), hm, nb8);
     nb8 = fma(mul(k(-4.0), uxy), g5, nb8);
     nb8 = fma(nuy_2, g6, nb8);
     nb8 = fma(nux_2, g7, nb8);

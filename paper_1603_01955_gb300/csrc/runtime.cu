@@ -204,6 +204,25 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+// Running sum over a thread's rows in the per-node type R: plain for FP64;
+// compensated (Kahan) for FP32, so that a sum of a few dozen FP32 terms keeps
+// FP32's precision and the FP64 pipe is touched once per thread, not per node.
+template <class R> struct RowSum {
+    R s = 0;
+    __device__ __forceinline__ void add(R v) { s += v; }
+    __device__ __forceinline__ double value() const { return (double)s; }
+};
+template <> struct RowSum<float> {
+    float s = 0, c = 0;
+    __device__ __forceinline__ void add(float v) {
+        const float y = __fsub_rn(v, c);
+        const float t = __fadd_rn(s, y);
+        c = __fsub_rn(__fsub_rn(t, s), y);
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
 // Per column: m(x) = sum_y rho u_x, centreline rho, sum_y u_x; the profiles at
 // one column; per block: partial sums of m, u_x, rho and a non-finite count.
 // Densities and velocities come from the post-collision populations of the
@@ -215,8 +234,10 @@ __global__ void __launch_bounds__(kObsCols* kObsRows)
                double ref0, double ref_slope, double gx, double gy, int prof_col, double isc) {
     // Per node in the storage's compute type (FP32 for FP32/16-bit storage,
     // whose values carry FP32 or coarser rounding already; FP64 for FP64),
-    // accumulated across nodes in FP64.  The mass flow needs no division:
-    // rho u_x = sum_i e_ix f~_i - rho F_x / 2.
+    // summed over the thread's rows in that type (compensated in FP32) and
+    // across threads in FP64.  The mass is n R(x) + sum of the density
+    // deviations, so the reference part is exact.  The mass flow needs no
+    // division: rho u_x = sum_i e_ix f~_i - rho F_x / 2.
     using R = RT<T>;
     __shared__ double sh[5][kObsRows][kObsCols];
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -225,6 +246,9 @@ __global__ void __launch_bounds__(kObsCols* kObsRows)
     if (x < nx) {
         const double ref = ref0 + ref_slope * x;
         const R hgx = R(0.5 * gx), hgy = R(0.5 * gy);
+        RowSum<R> sm, su, sd;
+        int rows = 0, nbad = 0;
+#pragma unroll 2
         for (int y = ty; y < ny; y += kObsRows) {
             const T* row = f + (long long)y * pitch + xoff + x;
             R v[9];
@@ -237,22 +261,26 @@ __global__ void __launch_bounds__(kObsCols* kObsRows)
             const R my = (v[2] - v[4]) + (a57 - a86) - hgy * rho;  // rho u_y
             const R irho = rcp(rho);
             const R ux = mx * irho, uy = my * irho;
-            if (!isfinite(rho) || !isfinite(ux) || !isfinite(uy)) bad += 1;
-            const double rho_d = ref + (double)drho;
-            m += (double)mx;
-            us += (double)ux;
-            mass += rho_d;
+            if (!isfinite(rho) || !isfinite(ux) || !isfinite(uy)) ++nbad;
+            sm.add(mx);
+            su.add(ux);
+            sd.add(drho);
+            ++rows;
             // centreline: the middle row, or the mean of the two middle rows
             if (ny & 1) {
-                if (y == (ny - 1) / 2) rc += rho_d;
+                if (y == (ny - 1) / 2) rc += ref + (double)drho;
             } else if (y == ny / 2 - 1 || y == ny / 2) {
-                rc += 0.5 * rho_d;
+                rc += 0.5 * (ref + (double)drho);
             }
             if (x == prof_col) {
                 obs[L.prof_x + y] = (double)ux;
                 obs[L.prof_y + y] = (double)uy;
             }
         }
+        m = sm.value();
+        us = su.value();
+        mass = rows * ref + sd.value();
+        bad = nbad;
     }
     sh[0][ty][tx] = m;
     sh[1][ty][tx] = us;
