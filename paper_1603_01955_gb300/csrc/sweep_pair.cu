@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(NC + 64, MB) sweep_pair_kernel(const SweepArgs
         pair_item(idx, Tn, a.ny, p.lag, level, y, tile);
         const T* stage = reinterpret_cast<const T*>(smem + s * G::STAGE_BYTES);
         T* dst = level ? static_cast<T*>(a.fout) : ring;
-        tile_update<T, MODE, V, G::SEG, true>(a, c, stage, tcx * V, tile * G::W + tcx * V, y,
+        tile_update<T, MODE, V, G::SEG, true, true>(a, c, stage, tcx * V, tile * G::W + tcx * V, y,
                                               empty + s, source(level), dst, level ? a.plane : p.ring_plane,
                                               level ? -1 : p.ring_rows - 1);
         mbar_arrive(stored + it % Q);

@@ -200,8 +200,10 @@ __device__ __forceinline__ void load_tile(const SweepArgs& a, const Field<T> f, 
 // field `dst` (periodic channels also write the halo columns -1 and nx).
 // c: the constants in the units of the stored values (SweepArgs::ks), so
 // 16-bit values are converted without a scale multiply.
+// kPackF32: collide FP32 storage two nodes per packed instruction as well
+// (the two-step sweep, whose HBM bytes per step are half the single step's).
 // kCG: `src` was written earlier in the same launch.
-template <class T, int MODE, int V, int SEG, bool kCG>
+template <class T, int MODE, int V, int SEG, bool kCG, bool kPackF32 = false>
 __device__ __forceinline__ void tile_update(const SweepArgs& a, const KC<typename Codec<T>::R>& c, const T* stage,
                                             int sv, int x0, int y, uint64_t* empty, const Field<T> src,
                                             T* dst, long long dst_plane, int dst_rmask) {
@@ -307,7 +309,7 @@ __device__ __forceinline__ void tile_update(const SweepArgs& a, const KC<typenam
     // FP32 sweep is bound by HBM alone: there the packed form finished its
     // arithmetic sooner but moved the bytes less evenly, and back-to-back
     // steps got slower, so it collides one node per lane.
-    if constexpr (Pair16<T>::ok && V % 2 == 0) {
+    if constexpr ((Pair16<T>::ok || kPackF32) && V % 2 == 0) {
 #pragma unroll
         for (int k = 0; k < V; k += 2) {
             float2 d[9];
