@@ -71,8 +71,9 @@ typedef struct {
     double s3, s8;  /* free relaxation rates; 1.1, 1.2 */
     double rho_out; /* outlet density (pressure drive) or mean density (body force); 1.0 */
     int storage;    /* clb_storage; CLB_FP32_SHIFTED */
-    int vec;        /* nodes per thread along x: FP64 1|2 (default 2), FP32 1|2|4 (4),
-                       16-bit 4|8 (4); 0 = default */
+    int vec;        /* nodes per thread along x of the direct sweep: FP64 1|2 (default 1),
+                       FP32 1|2|4 (default 1 below 196,608 nodes, else 4), 16-bit 4|8 (4);
+                       0 = default */
     int block_x;    /* threads per block, a multiple of 32 in 32..256; 0 = default 128 */
     void* stream;   /* cudaStream_t to queue work on; NULL = a stream owned by the library */
     /* Device allocator hooks (e.g. a framework's caching allocator); both NULL

@@ -494,7 +494,19 @@ clb_status clb_create(int nx, int ny, double kn, double a, double r, clb_drive d
         return fail(CLB_EINVAL, "clb_create: storage %d not available", o.storage);
     if ((o.alloc == nullptr) != (o.free == nullptr))
         return fail(CLB_EINVAL, "clb_create: alloc and free hooks must be given together");
-    int vec = o.vec ? o.vec : (o.storage == CLB_FP64 ? 2 : 4);
+    // Default nodes per thread of the direct sweep: one node per thread fills
+    // the GPU with more warps, which wins where the channel is small (latency
+    // bound) and for FP64 (FP64-pipe bound); four win for larger FP32 and for
+    // 16-bit channels (fewer instructions per byte).
+    int vec = o.vec;
+    if (!vec) {
+        if (o.storage == CLB_FP64)
+            vec = 1;
+        else if (o.storage == CLB_FP32_SHIFTED && (long long)nx * ny < (3LL << 16))
+            vec = 1;
+        else
+            vec = 4;
+    }
     if (!sweep_supported(o.storage, vec)) return fail(CLB_EINVAL, "clb_create: vec = %d not available", vec);
     int block_x = o.block_x ? o.block_x : 128;
     const int max_pipeline = 1 + tma_variant_count() + pair_variant_count();
