@@ -93,3 +93,14 @@ def test_default_engine(clb, storage, kn_mode, want):
     small = clb.Channel(4095, 256, 0.2, drive="pressure", drive_value=1.5, storage=storage, kn_mode=kn_mode)
     assert small.info()["pipeline"] == 1
     small.close()
+
+
+@pytest.mark.parametrize("storage,nx,ny,want", [("fp32s", 1601, 16, 1), ("fp32s", 767, 256, 1),
+                                                ("fp32s", 769, 256, 4), ("fp64", 1601, 16, 1),
+                                                ("fp64", 4097, 256, 1), ("fp16s", 1601, 16, 4)])
+def test_default_nodes_per_thread(clb, storage, nx, ny, want):
+    """The direct sweep's default nodes per thread: one for FP32 channels below
+    196,608 nodes and for FP64, four otherwise."""
+    ch = clb.Channel(nx, ny, 0.2, drive="pressure", drive_value=1.5, storage=storage)
+    assert ch.info()["vec"] == want
+    ch.close()
