@@ -67,6 +67,7 @@ struct SweepArgs {
     const void* rc_in;
     void* rc_out;
     int withhold_tile;        // testing: TMA tile whose inputs are never sent (-1: none)
+    int tile_order;           // TMA sweep: 0 = tiles from the first, 1 = from the last
     KC<float> kf;             // the constants above, derived, in FP32
     KC<double> kd;            // ... and in FP64
     // kf in the units of the stored values: every density-like constant times

@@ -672,6 +672,7 @@ static cudaError_t launch_single(clb_sim* s, SweepArgs& a, int mode, int cur) {
     a.fout = s->buf[cur ^ 1];
     a.rc_in = static_cast<const char*>(s->rc) + cur * rc_side;
     a.rc_out = static_cast<char*>(s->rc) + (cur ^ 1) * rc_side;
+    a.tile_order = cur;  // alternate the TMA sweep's tile order with the buffers
     const int tma_variant = pair_variant >= 0 ? pair_single_variant(pair_variant) : s->pipeline - 2;
     return s->pipeline >= 2 ? launch_sweep_tma(s->storage, mode, tma_variant, a, s->stream, s->status)
                             : launch_sweep(s->storage, mode, s->vec, s->block_x, a, s->stream);

@@ -60,23 +60,37 @@ __global__ void __launch_bounds__(NC + 32, MB) sweep_tma_kernel(const SweepArgs 
     asm volatile("griddepcontrol.wait;" ::: "memory");
 
     const int my_tiles = ntiles > (int)blockIdx.x ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    // Tile blockIdx.x + it * gridDim.x sits at row y, column tile xt; both
-    // advance by the grid's quotient and remainder, with no division per tile.
+    // Iteration it takes tile t = blockIdx.x + it * gridDim.x, or ntiles-1-t
+    // when a.tile_order is 1 (every other step: the rows the last sweep wrote
+    // last are read first, while many of them are still in L2).  The tile's
+    // row y and column tile xt move by the grid's quotient and remainder, with
+    // no division per tile.
+    const bool rev = a.tile_order != 0;
     const int y_step = (int)gridDim.x / tiles_per_row, xt_step = (int)gridDim.x % tiles_per_row;
     auto advance = [&](int& y, int& xt) {
-        xt += xt_step;
-        y += y_step;
-        if (xt >= tiles_per_row) {
-            xt -= tiles_per_row;
-            ++y;
+        if (!rev) {
+            xt += xt_step;
+            y += y_step;
+            if (xt >= tiles_per_row) {
+                xt -= tiles_per_row;
+                ++y;
+            }
+        } else {
+            xt -= xt_step;
+            y -= y_step;
+            if (xt < 0) {
+                xt += tiles_per_row;
+                --y;
+            }
         }
     };
+    const int t0 = rev ? ntiles - 1 - (int)blockIdx.x : (int)blockIdx.x;
 
     if (threadIdx.x >= NC) {
         // ---------------------------------------------------------- producer
         if (threadIdx.x != NC) return;
         int issued = 0;
-        int y = (int)blockIdx.x / tiles_per_row, xt = (int)blockIdx.x % tiles_per_row;
+        int y = t0 / tiles_per_row, xt = t0 % tiles_per_row;
         for (int it = 0; it < my_tiles; ++it, advance(y, xt)) {
             const int s = it % S;
             if (it >= S && !mbar_wait(empty + s, ((it / S) - 1) & 1)) {
@@ -98,7 +112,7 @@ __global__ void __launch_bounds__(NC + 32, MB) sweep_tma_kernel(const SweepArgs 
 
     // -------------------------------------------------------------- consumers
     const int tcx = threadIdx.x;
-    int y = (int)blockIdx.x / tiles_per_row, xt = (int)blockIdx.x % tiles_per_row;
+    int y = t0 / tiles_per_row, xt = t0 % tiles_per_row;
     for (int it = 0; it < my_tiles; ++it, advance(y, xt)) {
         const int s = it % S;
         if (!mbar_wait(full + s, (it / S) & 1)) {
