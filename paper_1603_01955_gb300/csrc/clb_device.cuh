@@ -32,20 +32,14 @@ template <> struct Codec<float> {
     static __device__ __forceinline__ float dec(float v, float) { return v; }
     static __device__ __forceinline__ float enc(float v, float) { return v; }
 };
-// unscale / prescale: the scaling of dec and enc alone, for callers that
-// convert two values per instruction.
 template <> struct Codec<__half> {
     using R = float;
-    static __device__ __forceinline__ float unscale(float v, float isc) { return __fmul_rn(v, isc); }
-    static __device__ __forceinline__ float prescale(float v, float sc) { return __fmul_rn(v, sc); }
     static __device__ __forceinline__ float dec(__half v, float isc) { return __fmul_rn(__half2float(v), isc); }
     static __device__ __forceinline__ __half enc(float v, float sc) { return __float2half_rn(__fmul_rn(v, sc)); }
 };
 // BF16 has FP32's exponent range, so its values are stored unscaled (scale 1).
 template <> struct Codec<__nv_bfloat16> {
     using R = float;
-    static __device__ __forceinline__ float unscale(float v, float) { return v; }
-    static __device__ __forceinline__ float prescale(float v, float) { return v; }
     static __device__ __forceinline__ float dec(__nv_bfloat16 v, float) { return __bfloat162float(v); }
     static __device__ __forceinline__ __nv_bfloat16 enc(float v, float) { return __float2bfloat16_rn(v); }
 };
