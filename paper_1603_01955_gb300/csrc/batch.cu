@@ -75,8 +75,11 @@ __device__ __forceinline__ void gather(const R* s, int nx, int ny, int x, int y,
     }
 }
 
+// two_buffers: the block holds two copies of its channel and alternates
+// between them, one barrier per step; otherwise it updates one copy in place,
+// with a barrier between the gather and the writes.
 template <class T, int NPT>
-__global__ void __launch_bounds__(512) batch_kernel(const BatchArgs a, int nsteps) {
+__global__ void __launch_bounds__(512) batch_kernel(const BatchArgs a, int nsteps, int two_buffers) {
     using R = T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* s = reinterpret_cast<R*>(smem_raw);
@@ -87,6 +90,7 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchArgs a, int nstep
     for (int k = threadIdx.x; k < 9 * nn; k += blockDim.x) s[k] = g[k];
     const R r = c.r, rc = c.rc, ref = c.ref0;
     __syncthreads();
+    R* out = two_buffers ? s + 9 * nn : s;
     for (int t = 0; t < nsteps; ++t) {
         R f[NPT][9];
 #pragma unroll
@@ -94,7 +98,7 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchArgs a, int nstep
             const int node = threadIdx.x + q * blockDim.x;
             if (node < nn) gather(s, nx, ny, node % nx, node / nx, r, rc, f[q]);
         }
-        __syncthreads();
+        if (!two_buffers) __syncthreads();
         if constexpr (std::is_same<R, float>::value && NPT % 2 == 0) {
             // two nodes per packed FP32 instruction (bit for bit the one-node collision)
 #pragma unroll
@@ -107,13 +111,13 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchArgs a, int nstep
                     collide<R, MODE_PERIODIC, float2>(d, ln::bc<float2>(ref), c);
 #pragma unroll
                     for (int i = 0; i < 9; ++i) {
-                        s[i * nn + n0] = d[i].x;
-                        s[i * nn + n1] = d[i].y;
+                        out[i * nn + n0] = d[i].x;
+                        out[i * nn + n1] = d[i].y;
                     }
                 } else if (n0 < nn) {
                     collide<R, MODE_PERIODIC>(f[q], ref, c);
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) s[i * nn + n0] = f[q][i];
+                    for (int i = 0; i < 9; ++i) out[i * nn + n0] = f[q][i];
                 }
             }
         } else {
@@ -123,11 +127,16 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchArgs a, int nstep
                 if (node < nn) {
                     collide<R, MODE_PERIODIC>(f[q], ref, c);
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) s[i * nn + node] = f[q][i];
+                    for (int i = 0; i < 9; ++i) out[i * nn + node] = f[q][i];
                 }
             }
         }
         __syncthreads();
+        if (two_buffers) {
+            R* t2 = s;
+            s = out;
+            out = t2;
+        }
     }
     for (int k = threadIdx.x; k < 9 * nn; k += blockDim.x) g[k] = s[k];
 }
@@ -202,6 +211,7 @@ struct clb_batch {
     size_t elem = 0;
     long long total = 0;  // elements of the state
     size_t smem = 0;      // bytes of shared memory per block
+    int two_buffers = 0;  // the block keeps two copies of its channel (when they fit)
     int max_nodes = 0;
     std::vector<BatchChannel> hch;
     std::vector<double> kn;
@@ -251,14 +261,14 @@ cudaError_t launch_batch(clb_batch* b, void* state, int block, int nsteps, cudaS
     const int npt = npt_for(b->max_nodes, block);
     dim3 grid(b->n), blk(block);
     switch (npt) {
-        case 1: batch_kernel<T, 1><<<grid, blk, b->smem, st>>>(a, nsteps); break;
-        case 2: batch_kernel<T, 2><<<grid, blk, b->smem, st>>>(a, nsteps); break;
+        case 1: batch_kernel<T, 1><<<grid, blk, b->smem, st>>>(a, nsteps, b->two_buffers); break;
+        case 2: batch_kernel<T, 2><<<grid, blk, b->smem, st>>>(a, nsteps, b->two_buffers); break;
         case 3:
-        case 4: batch_kernel<T, 4><<<grid, blk, b->smem, st>>>(a, nsteps); break;
+        case 4: batch_kernel<T, 4><<<grid, blk, b->smem, st>>>(a, nsteps, b->two_buffers); break;
         case 5:
         case 6:
         case 7:
-        case 8: batch_kernel<T, 8><<<grid, blk, b->smem, st>>>(a, nsteps); break;
+        case 8: batch_kernel<T, 8><<<grid, blk, b->smem, st>>>(a, nsteps, b->two_buffers); break;
         default: return cudaErrorInvalidConfiguration;
     }
     return cudaGetLastError();
@@ -359,7 +369,8 @@ clb_status clb_batch_create(int n, const int* nx, const int* ny, const double* k
     b->n = n;
     b->storage = o.storage;
     b->elem = elem;
-    b->smem = smem;
+    b->two_buffers = 2 * smem <= 200 * 1024;
+    b->smem = b->two_buffers ? 2 * smem : smem;
     b->max_nodes = max_nodes;
     b->alloc = o.alloc;
     b->dealloc = o.free;
@@ -417,7 +428,7 @@ clb_status clb_batch_create(int n, const int* nx, const int* ny, const double* k
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->dkd, kd.data(), n * sizeof(KC<double>), cudaMemcpyHostToDevice, b->stream);
     // initial state f^eq(rho_out, 0) = w_i rho_out: zero deviations (FP32) or w_i rho_out (FP64)
     if (e == cudaSuccess) e = cudaMemsetAsync(b->state, 0, b->total * elem, b->stream);
-    if (e == cudaSuccess) e = b->storage == CLB_FP64 ? set_smem_limit<double>(smem) : set_smem_limit<float>(smem);
+    if (e == cudaSuccess) e = b->storage == CLB_FP64 ? set_smem_limit<double>(b->smem) : set_smem_limit<float>(b->smem);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) {
         clb_batch_destroy(b);
