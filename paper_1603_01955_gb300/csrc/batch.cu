@@ -78,6 +78,68 @@ __device__ __forceinline__ void gather(const R* s, int nx, int ny, int x, int y,
 // two_buffers: the block holds two copies of its channel and alternates
 // between them, one barrier per step; otherwise it updates one copy in place,
 // with a barrier between the gather and the writes.
+// Where node (x, y) pulls its populations from (as gather above), as offsets
+// into the channel's [9][ny][nx] block, worked out once per launch: o[i] for
+// population i; at the walls f5, f6 (bottom) and f7, f8 (top) also take a
+// partner, wb / wt, with weight 1 - r.
+struct Pull {
+    int o[9];
+    int wb[2], wt[2];
+    bool bottom, top;
+};
+
+__device__ __forceinline__ Pull pull_of(int nx, int ny, int x, int y) {
+    Pull p;
+    const int nn = nx * ny;
+    const int xm = x == 0 ? nx - 1 : x - 1;
+    const int xp = x == nx - 1 ? 0 : x + 1;
+    auto at = [&](int i, int yy, int xx) { return i * nn + yy * nx + xx; };
+    p.bottom = y == 0;
+    p.top = y == ny - 1;
+    p.o[0] = at(0, y, x);
+    p.o[1] = at(1, y, xm);
+    p.o[3] = at(3, y, xp);
+    p.wb[0] = p.wb[1] = p.wt[0] = p.wt[1] = 0;
+    if (p.bottom) {
+        p.o[2] = at(4, 0, x);
+        p.o[5] = at(7, 0, x);
+        p.wb[0] = at(8, 0, xm);
+        p.o[6] = at(8, 0, x);
+        p.wb[1] = at(7, 0, xp);
+    } else {
+        p.o[2] = at(2, y - 1, x);
+        p.o[5] = at(5, y - 1, xm);
+        p.o[6] = at(6, y - 1, xp);
+    }
+    if (p.top) {
+        p.o[4] = at(2, y, x);
+        p.o[7] = at(5, y, x);
+        p.wt[0] = at(6, y, xp);
+        p.o[8] = at(6, y, x);
+        p.wt[1] = at(5, y, xm);
+    } else {
+        p.o[4] = at(4, y + 1, x);
+        p.o[7] = at(7, y + 1, xp);
+        p.o[8] = at(8, y + 1, xm);
+    }
+    return p;
+}
+
+// gather() through precomputed offsets (the same loads and arithmetic).
+template <class R>
+__device__ __forceinline__ void gather_at(const R* s, const Pull& p, R r, R rc, R (&f)[9]) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = s[p.o[i]];
+    if (p.bottom) {  // Eq. 20
+        f[5] = ln::fma(r, f[5], ln::mul(rc, s[p.wb[0]]));
+        f[6] = ln::fma(r, f[6], ln::mul(rc, s[p.wb[1]]));
+    }
+    if (p.top) {  // mirror of Eq. 20
+        f[7] = ln::fma(r, f[7], ln::mul(rc, s[p.wt[0]]));
+        f[8] = ln::fma(r, f[8], ln::mul(rc, s[p.wt[1]]));
+    }
+}
+
 template <class T, int NPT>
 __global__ void __launch_bounds__(512) batch_kernel(const BatchArgs a, int nsteps, int two_buffers) {
     using R = T;
@@ -91,12 +153,27 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchArgs a, int nstep
     const R r = c.r, rc = c.rc, ref = c.ref0;
     __syncthreads();
     R* out = two_buffers ? s + 9 * nn : s;
+    // with few nodes per thread, the pull offsets are worked out once
+    constexpr bool kPre = NPT <= 2;
+    Pull pl[kPre ? NPT : 1];
+    if constexpr (kPre) {
+#pragma unroll
+        for (int q = 0; q < NPT; ++q) {
+            const int node = threadIdx.x + q * blockDim.x;
+            pl[q] = pull_of(nx, ny, node % nx, node / nx);
+        }
+    }
     for (int t = 0; t < nsteps; ++t) {
         R f[NPT][9];
 #pragma unroll
         for (int q = 0; q < NPT; ++q) {
             const int node = threadIdx.x + q * blockDim.x;
-            if (node < nn) gather(s, nx, ny, node % nx, node / nx, r, rc, f[q]);
+            if (node < nn) {
+                if constexpr (kPre)
+                    gather_at(s, pl[q], r, rc, f[q]);
+                else
+                    gather(s, nx, ny, node % nx, node / nx, r, rc, f[q]);
+            }
         }
         if (!two_buffers) __syncthreads();
         if constexpr (std::is_same<R, float>::value && NPT % 2 == 0) {
