@@ -53,8 +53,8 @@ def measured_peaks() -> tuple[float, str]:
         return 6800.0, "fallback"
 
 
-def profiled_traffic(storage: str, pipeline: int):
-    """DRAM bytes per sweep launch from the committed ncu summary of that
+def profiled_value(storage: str, pipeline: int, key: str):
+    """A figure (`key: value` line) from the committed ncu summary of that
     engine, if it was taken on the current sweep sources (else None)."""
     kernel = "sweep" if pipeline <= 1 else "sweep_pair" if is_pair(pipeline) else "sweep_tma"
     path = os.path.join(ROOT, "profiles", f"{kernel}_{storage}_pressure_25601x256.md")
@@ -63,10 +63,35 @@ def profiled_traffic(storage: str, pipeline: int):
     except OSError:
         return None
     m_hash = re.search(r"sweep_source_sha256:\s*([0-9a-f]+)", text)
-    m_tr = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    if not m_hash or not m_tr or m_hash.group(1) != sweep_source_hash():
+    m_val = re.search(key + r":\s*([0-9.eE+]+)", text)
+    if not m_hash or not m_val or m_hash.group(1) != sweep_source_hash():
         return None
-    return float(m_tr.group(1))
+    return float(m_val.group(1))
+
+
+def profiled_traffic(storage: str, pipeline: int):
+    """DRAM bytes per sweep launch (ncu summary), or None."""
+    return profiled_value(storage, pipeline, "traffic_bytes_per_launch")
+
+
+def flops_block(clb, results):
+    """Measured arithmetic rate of each timed sweep: floating-point operations
+    per node update from the SASS counters in the committed ncu summary (None
+    where no summary of that kernel on the current sources exists) times the
+    measured node rate, against the fused multiply-add rate clb_peak_fma
+    measures in the sweep's compute precision (FP64 for FP64 storage, FP32
+    otherwise)."""
+    peaks = {"f32": clb.clb_peak_fma(clb.CLB_FP32_SHIFTED), "f64": clb.clb_peak_fma(clb.CLB_FP64)}
+    out = {"peak_tflops": {k: round(v, 3) for k, v in peaks.items()}, "peak_kind": "measured (clb_peak_fma)"}
+    for storage, r in results.items():
+        ops = profiled_value(storage, r["pipeline"], "fp_ops_per_node")
+        prec = "f64" if storage == "fp64" else "f32"
+        entry = {"precision": prec, "fp_ops_per_node": ops}
+        if ops is not None:
+            tf = ops * r["mlups"] * 1e6 / 1e12
+            entry.update(achieved_tflops=round(tf, 3), frac=round(tf / peaks[prec], 4))
+        out[storage] = entry
+    return out
 
 
 class ClockSampler:
@@ -297,6 +322,7 @@ def run_gpu(args):
             "kernel": engine_of(f32["pipeline"])["kernel"],
         },
         "variants": variants_block(results, nodes, peak),
+        "flops": flops_block(clb, results),
         "e2e": {
             "value": round(replica_mlups(nodes, K, t_e2e, world), 1),
             "unit": "MLUPS",

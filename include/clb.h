@@ -349,6 +349,21 @@ clb_status clb_observables_noalloc(const double* f_dev, int nx, int ny, int driv
                                    double* ux_prof, double* uy_prof, double* p_centre, double* dp_nonlin,
                                    double* m_of_x);
 
+/*
+ * clb_peak_fma - the GPU's fused multiply-add throughput in FP32
+ * (storage = CLB_FP32_SHIFTED) or FP64 (storage = CLB_FP64), in TFLOP/s
+ * (2 FLOP per fused multiply-add), measured by a short microbenchmark on the
+ * current device: every SM runs many independent chains of fused
+ * multiply-adds.  The paper has no counterpart; it is the compute peak the
+ * sweeps' measured FLOP rate is reported against.
+ *   stream   cudaStream_t to run on (NULL = legacy default stream); the call
+ *            synchronises it
+ *   tflops   output (host)
+ * Takes a few milliseconds (FP32) to some tens of milliseconds (FP64).
+ * Errors: CLB_EINVAL (storage not FP32_SHIFTED or FP64, tflops NULL), CLB_ECUDA.
+ */
+clb_status clb_peak_fma(int storage, void* stream, double* tflops);
+
 #ifdef __cplusplus
 }
 #endif

@@ -108,12 +108,13 @@ def _load():
                                         C.c_int64, C.c_int, C.POINTER(clb_opts), C.POINTER(P), D]
     lib.clb_adjoint_backward.argtypes = [P, C.c_double, D]
     lib.clb_adjoint_destroy.argtypes = [P]
+    lib.clb_peak_fma.argtypes = [C.c_int, P, D]
     for name in ("clb_create", "clb_step", "clb_observables", "clb_get_state", "clb_set_state",
                  "clb_info", "clb_sync", "clb_destroy", "clb_save", "clb_load", "clb_observables_noalloc",
                  "clb_batch_create",
                  "clb_batch_step", "clb_batch_tune", "clb_batch_observables", "clb_batch_get_state",
                  "clb_batch_set_state", "clb_batch_info", "clb_batch_destroy", "clb_adjoint_forward",
-                 "clb_adjoint_backward", "clb_adjoint_destroy"):
+                 "clb_adjoint_backward", "clb_adjoint_destroy", "clb_peak_fma"):
         getattr(lib, name).restype = C.c_int
     return lib
 
@@ -168,6 +169,13 @@ def clb_observables_noalloc(f_dev_ptr, nx, ny, drive, g, rho_in, rho_out, kn, pr
                                      C.byref(s) if s is not None else None, _dptr(ux_prof), _dptr(uy_prof),
                                      _dptr(p_centre), _dptr(dp_nonlin), _dptr(m_of_x))
     return _check(st) if check else st
+
+
+def clb_peak_fma(storage, stream_ptr=None) -> float:
+    """Measured fused multiply-add throughput (TFLOP/s) in FP32 (CLB_FP32_SHIFTED) or FP64."""
+    out = C.c_double()
+    _check(lib.clb_peak_fma(int(storage), C.c_void_p(stream_ptr) if stream_ptr else None, C.byref(out)))
+    return out.value
 
 
 def clb_get_state(sim, host_ptr):
