@@ -72,6 +72,29 @@ def test_steady_periodic_profile_closed_form(oracle_mod, ny, kn, kw):
     assert errs[1] < errs[0] / 5
 
 
+@pytest.mark.parametrize("ny,kn,kw", CASES)
+def test_slip_velocity_is_wall_extrapolation_of_closed_form(oracle_mod, ny, kn, kw):
+    """The slip velocity U_s of Sec. 3.1 is read as the node profile continued
+    linearly from the first two rows (J = 1, 2) to the wall at J = 1/2, the
+    mean of both walls.  On the steady periodic channel the node profile is
+    the closed-form parabola above, so U_s must equal 1.5 u(1) - 0.5 u(2) of
+    that parabola, which is its wall value u_s plus 9G/(8 tau) (a parabola is
+    not a line).  The residual is the same non-linear one as the profile's and
+    shrinks with G."""
+    errs = []
+    for G in (1e-5, 1e-6):
+        p, s = run_periodic(oracle_mod, 4, ny, kn, G, 8000, **kw)
+        sv, sq = oracle_mod.rates_kn(kn, ny)
+        tau = 1 / sv - 0.5
+        u_exact, us = closed_form_profile(G, ny, tau, 1 / sq - 0.5, p.c().r)
+        want = 1.5 * u_exact[0] - 0.5 * u_exact[1]
+        assert want == pytest.approx(us + 1.125 * G / tau, rel=1e-12)
+        got = s.observables()["u_slip"]
+        errs.append(abs(got - want) / want)
+    assert errs[0] < 1e-6
+    assert errs[1] < errs[0] / 5
+
+
 def test_slip_is_eq19_plus_G_tau_q(oracle_mod):
     """Second-order slip of Eq. 19, with lambda_e = Kn N/(1 + a Kn) (Eq. 16)
     and derivatives of the steady parabola at the wall, reproduces the

@@ -74,6 +74,11 @@ MUTANTS = [
     ("q_norm_sqrt_RT", "(3.0 * P_gx(p) * (double)ny * (double)ny * sqrt(1.0 / 6.0))",
      "(3.0 * P_gx(p) * (double)ny * (double)ny * sqrt(1.0 / 3.0))"),
     ("m_ns_constant", "(24.0 * mu * (1.0 / 3.0) * L)", "(12.0 * mu * (1.0 / 3.0) * L)"),
+    # slip velocity extrapolated to J = 0 instead of the wall at J = 1/2
+    ("slip_extrapolated_to_J0_bottom", "const real_t sb = 1.5 * ucol_prof[0] - 0.5 * ucol_prof[1];",
+     "const real_t sb = 2.0 * ucol_prof[0] - 1.0 * ucol_prof[1];"),
+    ("slip_extrapolated_to_J0_top", "const real_t st = 1.5 * ucol_prof[3] - 0.5 * ucol_prof[2];",
+     "const real_t st = 2.0 * ucol_prof[3] - 1.0 * ucol_prof[2];"),
     # complex-step derivative (the reference of the adjoint)
     ("complex_step_drops_r", "static real_t P_r(const oracle_params* p) { return p->r + I * p->r_im; }",
      "static real_t P_r(const oracle_params* p) { return p->r; }"),
