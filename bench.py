@@ -33,7 +33,7 @@ NX, NY, KN_OUT, RATIO = 25601, 256, 0.1, 2.47
 METRIC = "D2Q9 CLB MLUPS and % HBM roofline, FP32-shifted vs FP64 at stated error"
 WORKLOAD = "pressure-driven microchannel L/H=100, Ny=256 x Nx=25601 (6.55M nodes), Kn_out=0.1, p_in/p_out=2.47"
 SWEEP_SOURCES = ["paper_1603_01955_gb300/csrc/sweep.cu", "paper_1603_01955_gb300/csrc/sweep_tma.cu",
-                 "paper_1603_01955_gb300/csrc/sweep_pair.cu", "paper_1603_01955_gb300/csrc/tma_common.cuh",
+                 "paper_1603_01955_gb300/csrc/tma_common.cuh",
                  "paper_1603_01955_gb300/csrc/clb_device.cuh", "paper_1603_01955_gb300/csrc/clb_internal.h"]
 
 
@@ -56,7 +56,7 @@ def measured_peaks() -> tuple[float, str]:
 def profiled_value(storage: str, pipeline: int, key: str):
     """A figure (`key: value` line) from the committed ncu summary of that
     engine, if it was taken on the current sweep sources (else None)."""
-    kernel = "sweep" if pipeline <= 1 else "sweep_pair" if is_pair(pipeline) else "sweep_tma"
+    kernel = "sweep" if pipeline <= 1 else "sweep_tma"
     path = os.path.join(ROOT, "profiles", f"{kernel}_{storage}_pressure_25601x256.md")
     try:
         text = open(path).read()
@@ -303,9 +303,7 @@ def run_gpu(args):
             "workload": WORKLOAD,
             "nx": NX, "ny": NY, "kn_out": KN_OUT, "pressure_ratio": RATIO,
             "storage": "fp32s (deviations from w_i*rho_ref(x)), FP32 collide",
-            "step": ("one fused stream-collide sweep launch per two steps (two-step engine)"
-                     if is_pair(f32["pipeline"]) else "one fused stream-collide sweep per step")
-                    + "; one FP64 observable reduction per timed region",
+            "step": "one fused stream-collide sweep per step; one FP64 observable reduction per timed region",
             "l2": "no flush: each population buffer is 236 MB (FP32) / 472 MB (FP64), above the 129 MB L2",
             "parallelism": "replicas" if world > 1 else "single GPU",
             "launch": engine_of(f32["pipeline"]),
@@ -331,7 +329,7 @@ def run_gpu(args):
             "note": "per timed region: upload of the FP64 initial state from pinned host memory, K sweeps, "
                     "observables back to host; bytes per step = bytes per region / K",
         },
-        "gpu_launches": sweep_launches(K, f32["pipeline"]) + 2,
+        "gpu_launches": K + 2,
         "clocks": clocks,
     }
     if not args.no_batch:
@@ -451,35 +449,14 @@ def errors_vs_oracle(clb, variants, ref, steps):
     return out
 
 
-# tile shapes of the TMA-staged sweep: (consumer threads, nodes per thread, stages)
-TMA_SHAPES = [(128, 4, 4), (256, 4, 3), (256, 2, 4), (256, 2, 6), (256, 1, 8), (256, 4, 4), (224, 4, 3),
-              (128, 2, 8), (224, 4, 4), (512, 1, 4), (384, 1, 4), (384, 1, 6), (512, 2, 3)]
-
-
-# tile shapes of the two-step sweep (pipelines 15..19)
-PAIR_SHAPES = [(512, 2, 3), (256, 4, 3), (512, 1, 4), (256, 2, 4), (128, 4, 4)]
-
-
-def is_pair(pipeline: int) -> bool:
-    return pipeline >= 2 + len(TMA_SHAPES)
-
-
-def sweep_launches(steps: int, pipeline: int) -> int:
-    """Sweep kernels launched for `steps` time steps by the engine."""
-    return steps // 2 + steps % 2 if is_pair(pipeline) else steps
+# tile shapes of the TMA-staged sweep, pipelines 2 and 3: (consumer threads, nodes per thread, stages)
+TMA_SHAPES = [(512, 2, 3), (256, 4, 3)]
 
 
 def engine_of(pipeline: int) -> dict:
     if pipeline <= 1:
         return {"pipeline": pipeline, "engine": "direct vector loads + warp shuffles", "vec": 4, "block_x": 128,
                 "kernel": "sweep_kernel<float, pressure, 4>"}
-    if is_pair(pipeline):
-        nc, v, st = PAIR_SHAPES[pipeline - 2 - len(TMA_SHAPES)]
-        return {"pipeline": pipeline,
-                "engine": "two time steps per launch; TMA bulk copies into a shared-memory ring; the middle "
-                          "time level in a 32-row ring buffer held in L2",
-                "consumers": nc, "nodes_per_thread": v, "stages": st,
-                "kernel": f"sweep_pair_kernel<float, pressure, {nc}, {v}, {st}>"}
     nc, v, st = TMA_SHAPES[pipeline - 2]
     return {"pipeline": pipeline, "engine": "TMA bulk copies into a shared-memory ring",
             "consumers": nc, "nodes_per_thread": v, "stages": st,

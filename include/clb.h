@@ -83,15 +83,12 @@ typedef struct {
     void* alloc_ctx;
     /* How the sweep reads its inputs (FP32 and 16-bit storage; FP64 and
      * kn_mode 1 always 1): 0 = default (1 for channels below 2^20 nodes;
-     * larger ones 14 for FP32_SHIFTED, 3 for the 16-bit storages), 1 = direct
+     * larger ones 2 for FP32_SHIFTED, 3 for the 16-bit storages), 1 = direct
      * vector loads with warp shuffles (the only engine that vec and block_x
-     * configure), 2..14 = staged through shared memory by
-     * TMA bulk copies, tile shape 0..12 of the table in sweep_tma.cu (consumer
-     * threads x nodes per thread, ring stages), 15..19 = two time steps per
-     * launch with the middle time level kept in a 32-row ring that stays in
-     * L2 (tile shape 0..4 of the table in sweep_pair.cu; an odd last step
-     * runs the single-step TMA sweep of the same shape).  All give
-     * bit-identical results. */
+     * configure), 2..3 = staged through shared memory by TMA bulk copies,
+     * tile shape 0..1 of the table in sweep_tma.cu (2: 512 consumer threads x
+     * 2 nodes, 3 stages; 3: 256 x 4 nodes, 3 stages).  All give bit-identical
+     * results. */
     int pipeline;
     /* Local Knudsen number of a pressure channel (Sec. 3.2): 0 = from the
      * node's own pressure (default), 1 = from the centreline pressure p(x) of
@@ -99,15 +96,14 @@ typedef struct {
      * rows).  1 uses the direct-load sweep. */
     int kn_mode;
     /* Testing only: >= 0 makes the first TMA-staged sweep launch withhold the
-     * inputs of that tile (single-step engine) or work item (two-step
-     * engine), so that its bounded waits expire and the next clb_sync /
-     * clb_observables returns CLB_ETIMEOUT.  -1 (default) = off. */
+     * inputs of that tile, so that its bounded waits expire and the next
+     * clb_sync / clb_observables returns CLB_ETIMEOUT.  -1 (default) = off. */
     int test_withhold_tile;
     /* CUDA-graph replay of clb_step for channels whose sweeps are short
      * enough for launch overhead to matter: chunks of this many consecutive
      * sweeps are captured once (per buffer parity) and replayed.  0 =
      * default (64 for channels below 2^20 nodes, off above; off with the
-     * two-step engine and the testing option), < 0 = off, > 0 = chunk length.
+     * testing option), < 0 = off, > 0 = chunk length.
      * Results are identical with or without replay. */
     int graph_steps;
 } clb_opts;
@@ -185,7 +181,7 @@ typedef struct {
     int storage;          /* clb_storage */
     int vec, block_x;     /* launch shape of the sweep */
     int drive;            /* clb_drive */
-    double bytes_per_node;/* algorithmic HBM bytes per node update: 18 * element size (9 + 9 per step; 9 + 9 per two steps with the two-step engine) */
+    double bytes_per_node;/* algorithmic HBM bytes per node update: 18 * element size (9 reads + 9 writes) */
     double sv, sq;        /* s_v, s_q (Eq. 18, 21) at Kn (body force) or Kn_out (pressure) */
     double r;             /* r_b in use */
     double kn, a, g, rho_in, rho_out;

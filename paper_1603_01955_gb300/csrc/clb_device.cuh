@@ -343,31 +343,19 @@ __device__ __forceinline__ void collide(L (&d)[9], L ref, const KC<R>& c, const 
 // ------------------------------------------------- pressure boundary columns
 
 // A stored population field: element (i, y, x) at
-//   base + i * plane + (y & rmask) * pitch + xoff + x,
-// rmask = -1 for a whole buffer, 2^k - 1 for a ring of 2^k rows.
+//   base + i * plane + y * pitch + xoff + x.
 template <class T> struct Field {
     const T* base;
     long long plane;
-    int rmask;
 };
-
-// Read-only load (kCG = false: through the non-coherent path, for values
-// written before this launch) or an L2-coherent load (kCG = true: for values
-// other blocks wrote earlier in the same launch).
-template <bool kCG, class T> __device__ __forceinline__ T ld_field(const T* p) {
-    if constexpr (kCG)
-        return __ldcg(p);
-    else
-        return __ldg(p);
-}
 
 // Pre-collision deviations at one interior node (x in 1..nx-2) of a pressure
 // channel, gathered element by element; used only to rebuild the end columns.
-template <class T, class R, bool kCG = false>
+template <class T, class R>
 __device__ void gather_node(const SweepArgs& a, const KC<R>& c, const Field<T> f, int x, int y, R o[9]) {
     auto at = [&](int i, int dy, int xx) -> R {
-        const T* p = f.base + i * f.plane + (long long)((y + dy) & f.rmask) * a.pitch + a.xoff + xx;
-        return Codec<T>::dec(ld_field<kCG>(p), c.isc);
+        const T* p = f.base + i * f.plane + (long long)(y + dy) * a.pitch + a.xoff + xx;
+        return Codec<T>::dec(__ldg(p), c.isc);
     };
     const int rt = row_kind(y, a.ny);
     const R sha = c.sha, shd = c.shd;  // source at x-1; the source at x+1 gets the negative
@@ -402,13 +390,13 @@ __device__ void gather_node(const SweepArgs& a, const KC<R>& c, const Field<T> f
 // the first interior neighbour (a linear extrapolation of it as well would
 // amplify the shortest x-wavelength threefold and diverge at tau ~ 30).
 // Output: deviations relative to R(b).
-template <class T, class R, bool kCG = false>
+template <class T, class R>
 __device__ __forceinline__ void rebuild_column(const SweepArgs& a, const KC<R>& c, const Field<T> f, int x, int y,
                                             bool inlet, R* out) {
     const int dir = inlet ? 1 : -1;
     R n1[9], n2[9], e1[9], eb[9];
-    gather_node<T, R, kCG>(a, c, f, x + dir, y, n1);
-    gather_node<T, R, kCG>(a, c, f, x + 2 * dir, y, n2);
+    gather_node<T, R>(a, c, f, x + dir, y, n1);
+    gather_node<T, R>(a, c, f, x + 2 * dir, y, n2);
     R dr1, jx1, jy1, dr2, jx2, jy2;
     macro_dev(n1, dr1, jx1, jy1);
     macro_dev(n2, dr2, jx2, jy2);

@@ -113,25 +113,4 @@ cudaError_t launch_sweep_tma(int storage, int mode, int variant, const SweepArgs
                              unsigned* status);
 int tma_variant_count();
 
-// Two time steps per launch with the middle time level in a ring of rows
-// (sweep_pair.cu).
-struct PairArgs {
-    void* ring;                  // ring_rows rows x 9 planes, the buffers' pitch and xoff
-    long long ring_plane;        // elements per ring plane (= ring_rows * pitch)
-    int ring_rows;               // a power of two, > lag + 1
-    int tiles_per_row, grid;     // from plan_sweep_pair
-    int lag;                     // phases between a row's two levels (from plan_sweep_pair)
-    unsigned* done;              // [2 ny]: tiles completed per row, level 0 then level 1
-    unsigned long long epoch;    // launches since the counters were last cleared
-};
-constexpr int kPairRingRows = 32;
-// Tiles per row, grid size and lag of a two-step variant for a channel of nx columns.
-cudaError_t plan_sweep_pair(int storage, int mode, int variant, int nx, int* tiles_per_row, int* grid, int* lag);
-// Launch one two-step sweep: a.fin at time t -> a.fout at time t + 2.
-cudaError_t launch_sweep_pair(int storage, int mode, int variant, const SweepArgs& a, const PairArgs& p,
-                              cudaStream_t stream, unsigned* status);
-int pair_variant_count();
-// The single-step TMA variant with the same tile shape (for an odd last step).
-int pair_single_variant(int variant);
-
 }  // namespace clb

@@ -77,11 +77,8 @@ struct clb_sim {
     int cur = 0;            // buffer holding the last completed step
     double* obs = nullptr;  // device scratch of the observable reductions
     unsigned* status = nullptr;  // error bits of bounded device waits
-    int pipeline = 1;       // 1 direct loads, 2..14 TMA-staged variants, 15.. two-step variants
-    void* ring = nullptr;   // two-step engine: the middle time level (kPairRingRows rows)
-    void* pair_ctr = nullptr;  // two-step engine: 2 ny row counters
-    PairArgs pair{};
-    int withhold_tile = -1; // testing: TMA tile (work item) withheld in the first launch
+    int pipeline = 1;       // 1 direct loads, 2.. TMA-staged tile shapes
+    int withhold_tile = -1; // testing: TMA tile withheld in the first launch
     int graph_steps = 0;    // sweeps per replayed CUDA graph (0: no replay); even
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // per parity of `cur` at the chunk start
     int kn_mode = 0;        // 1: centreline Knudsen number (pressure channel)
@@ -459,8 +456,6 @@ clb_status clb_destroy(clb_sim* s) {
     s->dfree(s->obs);
     s->dfree(s->status);
     s->dfree(s->rc);
-    s->dfree(s->ring);
-    s->dfree(s->pair_ctr);
     for (cudaGraphExec_t g : s->graph)
         if (g) cudaGraphExecDestroy(g);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
@@ -509,7 +504,7 @@ clb_status clb_create(int nx, int ny, double kn, double a, double r, clb_drive d
     }
     if (!sweep_supported(o.storage, vec)) return fail(CLB_EINVAL, "clb_create: vec = %d not available", vec);
     int block_x = o.block_x ? o.block_x : 128;
-    const int max_pipeline = 1 + tma_variant_count() + pair_variant_count();
+    const int max_pipeline = 1 + tma_variant_count();
     if (o.pipeline < 0 || o.pipeline > max_pipeline)
         return fail(CLB_EINVAL, "clb_create: pipeline = %d must be 0..%d", o.pipeline, max_pipeline);
     if (o.kn_mode < 0 || o.kn_mode > 1) return fail(CLB_EINVAL, "clb_create: kn_mode = %d must be 0 or 1", o.kn_mode);
@@ -526,8 +521,9 @@ clb_status clb_create(int nx, int ny, double kn, double a, double r, clb_drive d
     s->kn_mode = (drive == CLB_DRIVE_PRESSURE) ? o.kn_mode : 0;
     s->withhold_tile = o.test_withhold_tile;
     // Default engine: the TMA tile shape that was fastest on the 25601 x 256
-    // pressure channel for the storage (512 x 2 nodes, 3 stages for FP32;
-    // 256 x 4 nodes, 3 stages for 16-bit).  Below 2^20 nodes, where a step is
+    // pressure channel for the storage (pipeline 2: 512 x 2 nodes, 3 stages,
+    // for FP32; pipeline 3: 256 x 4 nodes, 3 stages, for 16-bit).  Below 2^20
+    // nodes, where a step is
     // bound by its latency rather than by HBM, the direct-load sweep is faster
     // (801 x 8: 4.1 against 4.7 us; 6401 x 64: 6.4 against 7.5 us per step),
     // and from 12801 x 128 up the TMA sweep is.  FP64 and the centreline
@@ -539,15 +535,15 @@ clb_status clb_create(int nx, int ny, double kn, double a, double r, clb_drive d
     else if ((long long)nx * ny < (1LL << 20))
         s->pipeline = 1;  // small channels: the direct sweep has the shorter latency per step
     else
-        s->pipeline = (o.storage == CLB_FP32_SHIFTED) ? 14 : 3;
+        s->pipeline = (o.storage == CLB_FP32_SHIFTED) ? 2 : 3;
     {
-        // graph replay: not with the two-step engine (cooperative launches) or the testing option
+        // graph replay: not with the testing option
         int k = 0;
         if (o.graph_steps > 0)
             k = o.graph_steps;
         else if (o.graph_steps == 0)
             k = ((long long)nx * ny < (1LL << 20)) ? 64 : 0;
-        if (s->pipeline > 1 + tma_variant_count() || o.test_withhold_tile >= 0) k = 0;
+        if (o.test_withhold_tile >= 0) k = 0;
         s->graph_steps = k + (k & 1);  // even: a chunk ends on the buffer it started from
     }
     s->yc0 = (ny % 2) ? (ny - 1) / 2 : ny / 2 - 1;
@@ -617,28 +613,6 @@ clb_status clb_create(int nx, int ny, double kn, double a, double r, clb_drive d
         clb_destroy(s);
         return fail(CLB_ENOMEM, "clb_create: device allocation of %zu bytes failed", 2 * s->buf_bytes);
     }
-    const int pair_variant = s->pipeline - 2 - tma_variant_count();
-    if (pair_variant >= 0) {
-        PairArgs& p = s->pair;
-        p.ring_rows = kPairRingRows;
-        p.ring_plane = (long long)p.ring_rows * s->pitch;
-        const int mode = drive == CLB_DRIVE_PRESSURE ? MODE_PRESSURE : MODE_PERIODIC;
-        cudaError_t e = plan_sweep_pair(o.storage, mode, pair_variant, nx, &p.tiles_per_row, &p.grid, &p.lag);
-        if (e != cudaSuccess) {
-            clb_destroy(s);
-            return fail(CLB_ECUDA, "clb_create: two-step sweep: %s", cudaGetErrorString(e));
-        }
-        s->ring = s->dalloc((size_t)9 * p.ring_plane * s->elem);
-        s->pair_ctr = s->dalloc((size_t)8 * ny);
-        if (!s->ring || !s->pair_ctr) {
-            clb_destroy(s);
-            return fail(CLB_ENOMEM, "clb_create: device allocation of the two-step ring failed");
-        }
-        p.ring = s->ring;
-        p.done = static_cast<unsigned*>(s->pair_ctr);
-        p.epoch = 0;
-    }
-
     clb_status st = CLB_OK;
     auto chk = [&](cudaError_t e, const char* what) {
         if (e != cudaSuccess && st == CLB_OK) st = fail(CLB_ECUDA, "clb_create: %s: %s", what, cudaGetErrorString(e));
@@ -647,10 +621,6 @@ clb_status clb_create(int nx, int ny, double kn, double a, double r, clb_drive d
     chk(cudaMemsetAsync(s->buf[1], 0, s->buf_bytes, s->stream), "memset");
     chk(cudaMemsetAsync(s->obs, 0, s->L.total * sizeof(double), s->stream), "memset");
     chk(cudaMemsetAsync(s->status, 0, sizeof(unsigned), s->stream), "memset");
-    if (s->ring) {
-        chk(cudaMemsetAsync(s->ring, 0, (size_t)9 * s->pair.ring_plane * s->elem, s->stream), "memset");
-        chk(cudaMemsetAsync(s->pair_ctr, 0, (size_t)8 * ny, s->stream), "memset");
-    }
     const double rho_slope = (drive == CLB_DRIVE_PRESSURE) ? (s->rho_out - s->rho_in) / (double)(nx - 1) : 0.0;
     chk(cudaMemsetAsync(s->rc, 0, (size_t)4 * s->rc_stride * (o.storage == CLB_FP64 ? 8 : 4), s->stream), "memset");
     chk(launch_init(s, s->buf[0], s->rho_in, rho_slope), "init");
@@ -664,17 +634,15 @@ clb_status clb_create(int nx, int ny, double kn, double a, double r, clb_drive d
     return CLB_OK;
 }
 
-// One single-step sweep launch from buffer `cur` (direct or TMA engine).
+// One sweep launch from buffer `cur` (direct or TMA engine).
 static cudaError_t launch_single(clb_sim* s, SweepArgs& a, int mode, int cur) {
     const size_t rc_side = (size_t)2 * s->rc_stride * (s->storage == CLB_FP64 ? 8 : 4);
-    const int pair_variant = s->pipeline - 2 - tma_variant_count();
     a.fin = s->buf[cur];
     a.fout = s->buf[cur ^ 1];
     a.rc_in = static_cast<const char*>(s->rc) + cur * rc_side;
     a.rc_out = static_cast<char*>(s->rc) + (cur ^ 1) * rc_side;
     a.tile_order = cur;  // alternate the TMA sweep's tile order with the buffers
-    const int tma_variant = pair_variant >= 0 ? pair_single_variant(pair_variant) : s->pipeline - 2;
-    return s->pipeline >= 2 ? launch_sweep_tma(s->storage, mode, tma_variant, a, s->stream, s->status)
+    return s->pipeline >= 2 ? launch_sweep_tma(s->storage, mode, s->pipeline - 2, a, s->stream, s->status)
                             : launch_sweep(s->storage, mode, s->vec, s->block_x, a, s->stream);
 }
 
@@ -703,17 +671,6 @@ clb_status clb_step(clb_sim* s, int64_t n) {
     if (n < 0) return fail(CLB_EINVAL, "clb_step: n < 0");
     const int mode = s->drive == CLB_DRIVE_PRESSURE ? MODE_PRESSURE : MODE_PERIODIC;
     SweepArgs a = make_args(s);
-    const int pair_variant = s->pipeline - 2 - tma_variant_count();
-    for (; pair_variant >= 0 && n >= 2; n -= 2) {
-        a.fin = s->buf[s->cur];
-        a.fout = s->buf[s->cur ^ 1];
-        cudaError_t e = launch_sweep_pair(s->storage, mode, pair_variant, a, s->pair, s->stream, s->status);
-        if (e != cudaSuccess) return fail(CLB_ECUDA, "clb_step: two-step sweep launch: %s", cudaGetErrorString(e));
-        ++s->pair.epoch;
-        s->cur ^= 1;
-        s->step += 2;
-        s->withhold_tile = a.withhold_tile = -1;  // the testing option acts on the first launch only
-    }
     // replayed chunks (the chunk length is even, so `cur` is where it started)
     for (; s->graph_steps > 0 && n >= s->graph_steps; n -= s->graph_steps) {
         if (!s->graph[s->cur]) {
@@ -741,11 +698,6 @@ static clb_status check_status(clb_sim* s, const char* who) {
     CUDA_OR(cudaStreamSynchronize(s->stream));
     if (st) {
         CUDA_OR(cudaMemsetAsync(s->status, 0, sizeof(unsigned), s->stream));
-        if (s->pair_ctr) {  // the two-step counters are stale after a launch gave up
-            CUDA_OR(cudaMemsetAsync(s->pair_ctr, 0, (size_t)8 * s->ny, s->stream));
-            CUDA_OR(cudaStreamSynchronize(s->stream));
-            s->pair.epoch = 0;
-        }
         return fail(CLB_ETIMEOUT, "%s: a sweep gave up waiting for its staged inputs (bits %u)", who, st);
     }
     return CLB_OK;
@@ -766,9 +718,8 @@ clb_status clb_info(const clb_sim* s, clb_info_t* info) {
     info->vec = s->vec;
     info->block_x = s->block_x;
     info->drive = s->drive;
-    // HBM bytes per node update: one read and one write of the nine
-    // populations per launch; the two-step engine does two updates per launch
-    info->bytes_per_node = 18.0 * (double)s->elem / (s->ring ? 2.0 : 1.0);
+    // HBM bytes per node update: one read and one write of the nine populations
+    info->bytes_per_node = 18.0 * (double)s->elem;
     info->sv = s->sv;
     info->sq = s->sq;
     info->r = s->r;

@@ -18,9 +18,9 @@
 // thread loads each plane as one 8/16-byte vector; the populations that move
 // along x arrive from the neighbouring lane by a warp shuffle, and only lanes 0
 // and 31 load the one element across the warp edge.  The wall rows are whole
-// blocks, so the wall branch never diverges inside a warp.  Boundary nodes of
-// a pressure channel are found through the column-type mask and rebuilt before
-// their collision.  No value is read twice from DRAM: every population of the
+// blocks, so the wall branch never diverges inside a warp.  The inlet and
+// outlet columns of a pressure channel are recognised from their indices
+// (x = 0 and x = nx - 1) and rebuilt before their collision.  No value is read twice from DRAM: every population of the
 // last step is pulled by exactly one node.
 #include <cstdint>
 #include <type_traits>
@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) sweep_kernel(const S
         const int kin = kfirst, kout = klast;
         if (kin >= 0) {
             R t[9];
-            rebuild_column<T, R>(a, c, Field<T>{fin, a.plane, -1}, x0 + kin, y, true, t);
+            rebuild_column<T, R>(a, c, Field<T>{fin, a.plane}, x0 + kin, y, true, t);
 #pragma unroll
             for (int k = 0; k < V; ++k)
                 if (k == kin)
@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) sweep_kernel(const S
         }
         if (kout >= 0) {
             R t[9];
-            rebuild_column<T, R>(a, c, Field<T>{fin, a.plane, -1}, x0 + kout, y, false, t);
+            rebuild_column<T, R>(a, c, Field<T>{fin, a.plane}, x0 + kout, y, false, t);
 #pragma unroll
             for (int k = 0; k < V; ++k)
                 if (k == kout)

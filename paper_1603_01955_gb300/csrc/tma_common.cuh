@@ -1,6 +1,6 @@
-// Pieces shared by the TMA-staged sweeps (sweep_tma.cu: one time step per
-// launch; sweep_pair.cu: two): mbarrier and bulk-copy wrappers, the tile
-// geometry, and one consumer thread's update of its nodes of a staged tile.
+// Pieces of the TMA-staged sweep (sweep_tma.cu): mbarrier and bulk-copy
+// wrappers, the tile geometry, and one consumer thread's update of its nodes
+// of a staged tile.
 //
 // A tile is a row segment of W = NC*V columns.  Its inputs are nine segments,
 // one per direction i, taken from the row the population is pulled from
@@ -77,27 +77,6 @@ __device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t b
 __device__ __forceinline__ void fence_barrier_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
-
-// Orders this thread's generic-proxy global accesses with later (or, on the
-// writing side, other threads' later) bulk copies of the same memory.
-__device__ __forceinline__ void fence_proxy_async_global() {
-    asm volatile("fence.proxy.async.global;" ::: "memory");
-}
-
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
-    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Barrier 1 among the first n threads of the block (n a multiple of 32).  The
-// non-aligned form: the threads of a warp may arrive at different times (some
-// leave a tile early, each leaves a spin wait on its own).
-__device__ __forceinline__ void named_sync(int n) { asm volatile("barrier.sync 1, %0;" ::"r"(n) : "memory"); }
 
 template <class T, int V> struct VecT;
 template <> struct VecT<float, 4> { using type = float4; };
@@ -184,7 +163,7 @@ __device__ __forceinline__ void load_tile(const SweepArgs& a, const Field<T> f, 
     const uint32_t bytes = (uint32_t)n_el * sizeof(T);
     mbar_arrive_expect_tx(full, 9 * bytes);
     for (int i = 0; i < 9; ++i) {
-        const T* src = f.base + seg_plane(i, rt) * f.plane + (long long)((y + seg_dy(i, rt)) & f.rmask) * a.pitch + first;
+        const T* src = f.base + seg_plane(i, rt) * f.plane + (long long)(y + seg_dy(i, rt)) * a.pitch + first;
         bulk_copy(stage + i * SEG * (int)sizeof(T), src, bytes, full);
     }
 }
@@ -200,13 +179,10 @@ __device__ __forceinline__ void load_tile(const SweepArgs& a, const Field<T> f, 
 // field `dst` (periodic channels also write the halo columns -1 and nx).
 // c: the constants in the units of the stored values (SweepArgs::ks), so
 // 16-bit values are converted without a scale multiply.
-// kPackF32: collide FP32 storage two nodes per packed instruction as well
-// (the two-step sweep, whose HBM bytes per step are half the single step's).
-// kCG: `src` was written earlier in the same launch.
-template <class T, int MODE, int V, int SEG, bool kCG, bool kPackF32 = false>
+template <class T, int MODE, int V, int SEG>
 __device__ __forceinline__ void tile_update(const SweepArgs& a, const KC<typename Codec<T>::R>& c, const T* stage,
                                             int sv, int x0, int y, uint64_t* empty, const Field<T> src,
-                                            T* dst, long long dst_plane, int dst_rmask) {
+                                            T* dst) {
     using R = typename Codec<T>::R;
     const int rt = row_kind(y, a.ny);
     constexpr int E = 16 / (int)sizeof(T);
@@ -286,7 +262,7 @@ __device__ __forceinline__ void tile_update(const SweepArgs& a, const KC<typenam
         const int kin = kfirst, kout = klast;  // inlet x = 0, outlet x = nx - 1
         if (kin >= 0) {
             R t[9];
-            rebuild_column<T, R, kCG>(a, c, src, x0 + kin, y, true, t);
+            rebuild_column<T, R>(a, c, src, x0 + kin, y, true, t);
 #pragma unroll
             for (int k = 0; k < V; ++k)
                 if (k == kin)
@@ -295,7 +271,7 @@ __device__ __forceinline__ void tile_update(const SweepArgs& a, const KC<typenam
         }
         if (kout >= 0) {
             R t[9];
-            rebuild_column<T, R, kCG>(a, c, src, x0 + kout, y, false, t);
+            rebuild_column<T, R>(a, c, src, x0 + kout, y, false, t);
 #pragma unroll
             for (int k = 0; k < V; ++k)
                 if (k == kout)
@@ -309,7 +285,7 @@ __device__ __forceinline__ void tile_update(const SweepArgs& a, const KC<typenam
     // FP32 sweep is bound by HBM alone: there the packed form finished its
     // arithmetic sooner but moved the bytes less evenly, and back-to-back
     // steps got slower, so it collides one node per lane.
-    if constexpr ((Pair16<T>::ok || kPackF32) && V % 2 == 0) {
+    if constexpr (Pair16<T>::ok && V % 2 == 0) {
 #pragma unroll
         for (int k = 0; k < V; k += 2) {
             float2 d[9];
@@ -338,8 +314,8 @@ __device__ __forceinline__ void tile_update(const SweepArgs& a, const KC<typenam
             for (int i = 0; i < 9; ++i) f[i][k] = d[i];
         }
     }
-    const long long P = dst_plane;
-    T* orow = dst + (long long)(y & dst_rmask) * a.pitch + a.xoff;
+    const long long P = a.plane;
+    T* orow = dst + (long long)y * a.pitch + a.xoff;
     if (x0 + V <= a.nx) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) {

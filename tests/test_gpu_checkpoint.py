@@ -26,7 +26,7 @@ CASES = [
     # (storage, drive, kn_mode, pipeline of the saved run, pipeline of the resumed run)
     ("fp64", "pressure", 0, 0, 0),
     ("fp32s", "pressure", 0, 0, 1),
-    ("fp32s", "body_force", 0, 14, 16),
+    ("fp32s", "body_force", 0, 2, 3),
     ("fp16s", "pressure", 0, 0, 0),
     ("bf16s", "body_force", 0, 0, 2),
     ("fp32s", "pressure", 1, 0, 0),
