@@ -47,7 +47,7 @@ def run(kn: float, threads: int) -> dict:
         s.step(CHECK, threads)
         steps += CHECK
         m = s.observables()["mass_flow"]
-        res = abs(m - prev) / abs(m)
+        res = float(abs(m - prev) / abs(m))
         prev = m
         if res < TOL:
             break
@@ -56,14 +56,14 @@ def run(kn: float, threads: int) -> dict:
     return {
         "kn_out": kn,
         "steps": steps,
-        "residual": res,
-        "converged": res < TOL,
+        "residual": float(res),
+        "converged": bool(res < TOL),
         "oracle_seconds": round(time.perf_counter() - t0, 1),
-        "mass_flow": o["mass_flow"],
-        "q_norm": o["q_norm"],
-        "u_slip": o["u_slip"],
-        "ux_max": o["ux_max"],
-        "total_mass": o["total_mass"],
+        "mass_flow": float(o["mass_flow"]),
+        "q_norm": float(o["q_norm"]),
+        "u_slip": float(o["u_slip"]),
+        "ux_max": float(o["ux_max"]),
+        "total_mass": float(o["total_mass"]),
         "ux_prof_outlet": [float(v) for v in o["ux_prof"]],
         "cols": COLS,
         "dp_nonlin": [float(o["dp_nonlin"][x]) for x in COLS],

@@ -3,16 +3,22 @@
 Knudsen number from the centreline pressure, L/H = 100 (ny = 8, nx = 801),
 run to steady state for several outlet Knudsen numbers.  The experimental
 and analytical curves the paper compares with are not available, so the
-checks are the properties the method must show: a uniform mass flow along
-the channel, and S = m/m_ns above 1 (slip) and growing with Kn_out.  The
+checks are the properties the method must show (a uniform mass flow along
+the channel, and S = m/m_ns above 1 and growing with Kn_out) and, value by
+value, the FP64 oracle's steady S at the same step count
+(tests/golden/mass_flow_curve_801x8.json, written by the oracle alone).  The
 paper's second abscissa is Kn_ave = (Kn_in + Kn_out)/2 with
 Kn_in = Kn_out p_out/p_in."""
+import json
+import os
+
 import numpy as np
 import pytest
 
 pytestmark = pytest.mark.gpu
 
 KN_OUT = (0.02, 0.05, 0.1, 0.2, 0.4)
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "mass_flow_curve_801x8.json")
 
 
 @pytest.fixture(scope="module")
@@ -54,3 +60,21 @@ def test_mass_flow_rate_curve(clb):
     # Kn_ave of the paper's second plot: the inlet Knudsen number is Kn_out p_out/p_in
     kn_ave = 0.5 * (np.array(KN_OUT) / 1.8 + np.array(KN_OUT))
     assert np.allclose(kn_ave, np.array(KN_OUT) * (1 + 1 / 1.8) / 2)
+
+
+def test_steady_S_matches_oracle(clb):
+    """S on the GPU after exactly the steps the FP64 oracle took to reach a
+    change below 1e-11 per 1000 steps, against the oracle's S there."""
+    with open(GOLDEN) as f:
+        cases = json.load(f)["cases"]
+    assert [c["kn_out"] for c in cases] == list(KN_OUT)
+    for c in cases:
+        assert c["converged"]
+        ch = clb.Channel(801, 8, c["kn_out"], sigma=0.93, drive="pressure", drive_value=1.8, storage="fp64",
+                         kn_mode=1)
+        ch.step(c["steps"])
+        o = ch.observables()
+        ch.close()
+        assert o["q_norm"] == pytest.approx(c["S"], rel=1e-10), c["kn_out"]
+        assert o["mass_flow"] == pytest.approx(c["mass_flow"], rel=1e-10), c["kn_out"]
+        assert o["u_slip"] == pytest.approx(c["u_slip"], rel=1e-9), c["kn_out"]
