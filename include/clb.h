@@ -240,28 +240,49 @@ clb_status clb_load(const char* path, const clb_opts* opts, clb_sim** out);
 /* ------------------------------------------------------------------------
  * Batched Knudsen sweep (Sec. 3.1, Fig. 2): many periodic body-force channels
  * of uneven height and Knudsen number advanced together.  Each channel lives
- * in the shared memory of one thread block for many steps (one persistent
+ * in the shared memory of a thread block for many steps (one persistent
  * launch per chunk of steps, replayed from a CUDA graph), so the channel must
  * fit: 9 * nx * ny * element size <= 200 KB.  Every channel uses the same a,
  * r_b, G and opts (s3, s8, B2, sigma, rho_out); its rates s_v, s_q come from
  * its own Kn and ny (Eq. 18, 21).  The arithmetic per node is that of
  * clb_step on a periodic channel.
+ *
+ * Schedule: each channel is updated by a warp-aligned range of one block's
+ * threads, each thread taking 1, 2, 4 or 8 nodes; unpacked, every channel has
+ * a block of its own; packed, small channels share blocks (first fit by
+ * decreasing width, within 200 KB of shared memory per block).  Every
+ * schedule gives the same bits.
  * ------------------------------------------------------------------------ */
 typedef struct clb_batch clb_batch; /* opaque */
 
 /* n channels; nx[k], ny[k], kn[k] per channel (host arrays).  opts->storage
- * CLB_FP64 or CLB_FP32_SHIFTED; opts->block_x 0 = autotuned on the first
- * clb_batch_step (or by clb_batch_tune), else threads per block (32..512).
- * Initial state f^eq(rho_out, 0).  Errors: CLB_EINVAL, CLB_ENOMEM, CLB_ECUDA. */
+ * CLB_FP64 or CLB_FP32_SHIFTED; opts->block_x 0 = schedule autotuned on the
+ * first clb_batch_step (or by clb_batch_tune), else that many threads per
+ * block (32..512), one channel per block, nodes per thread the fewest of 1,
+ * 2, 4, 8 that fit.  Initial state f^eq(rho_out, 0).
+ * Errors: CLB_EINVAL, CLB_ENOMEM, CLB_ECUDA. */
 clb_status clb_batch_create(int n, const int* nx, const int* ny, const double* kn, double a, double r, double g,
                             const clb_opts* opts, clb_batch** out);
 
 /* Advance every channel n >= 0 steps (queued on the batch's stream). */
 clb_status clb_batch_step(clb_batch* b, int64_t n);
 
-/* Time each candidate block size (64..512 threads) on a copy of the state and
- * keep the fastest; the state itself does not advance.  Synchronises. */
+/* Autotuner: time every feasible schedule (nodes per thread 1, 2, 4, 8,
+ * each unpacked and packed) for 200 steps on a copy of the state and keep
+ * the fastest; the state itself does not advance.  *block_x_out (may be NULL)
+ * receives the chosen threads per block.  Synchronises. */
 clb_status clb_batch_tune(clb_batch* b, int* block_x_out);
+
+/* Use the schedule with nodes_per_thread (1, 2, 4 or 8) and packing
+ * (0 = one channel per block, 1 = packed) instead of the tuner's choice.
+ * Synchronises.  Errors: CLB_EINVAL (a value out of range, or a channel
+ * needs more than 512 threads at that many nodes per thread). */
+clb_status clb_batch_set_schedule(clb_batch* b, int nodes_per_thread, int packed);
+
+/* The schedule in use (each output may be NULL): threads per block, nodes
+ * per thread, blocks per launch, packed (0/1). */
+clb_status clb_batch_schedule(const clb_batch* b, int* threads_per_block, int* nodes_per_thread, int* blocks,
+                              int* packed);
 
 /* Per-channel scalars into s[n] (mass_flow, q_norm = Q of Sec. 3.1, u_slip at
  * column 0, total_mass, step; residual and ux_max are not computed: -1, 0).
@@ -298,9 +319,22 @@ clb_status clb_adjoint_forward(int nx, int ny, double kn, double a, double r, do
                                int checkpoint_every, const clb_opts* opts, clb_adjoint** out, double* J);
 
 /* grad[0..2] = seed * dJ/d(r_b, a, G), walking the checkpointed forward pass
- * backwards (recomputing each segment).  May be called repeatedly.
- * Synchronises. */
+ * backwards (recomputing each segment).  May be called repeatedly; the
+ * parameter sums are taken per thread block and added in a fixed order, so
+ * repeated calls give the same bits.  Synchronises. */
 clb_status clb_adjoint_backward(clb_adjoint* h, double seed, double grad[3]);
+
+/* The normalised flow rate of Sec. 3.1 after the forward pass,
+ * Q = J / (F H^2 sqrt(RT/2) / p) with RT = 1/3, p = rho0 RT, F = rho0 G, H = ny,
+ * that is Q = J / (3 G ny^2 sqrt(1/6)).  No device work.
+ * Errors: CLB_EINVAL (NULL argument, or G = 0). */
+clb_status clb_adjoint_q(const clb_adjoint* h, double* q);
+
+/* grad[0..2] = seed * dQ/d(r_b, a, G): the adjoint gradient of J (as
+ * clb_adjoint_backward) divided by the normalisation, and for G also the
+ * normalisation's own term -Q/G.  May be called repeatedly; synchronises.
+ * Errors: CLB_EINVAL (NULL argument, or G = 0), CLB_ECUDA. */
+clb_status clb_adjoint_q_backward(clb_adjoint* h, double seed, double grad[3]);
 
 /* Release everything; NULL is accepted. */
 clb_status clb_adjoint_destroy(clb_adjoint* h);
@@ -334,7 +368,9 @@ clb_status clb_adjoint_destroy(clb_adjoint* h);
  * the maximum sizes above), which every GPU that loads the library holds until
  * the process exits.  The first call on a device looks up that array's device
  * address (cudaGetSymbolAddress) with the device current; make that first call
- * before any stream capture.  All calls on a device share the array: calls that
+ * before any stream capture.  The address is kept for the life of the process:
+ * after cudaDeviceReset (or anything else that destroys the device's primary
+ * context) it is stale, so do not call this entry point on that device again.  All calls on a device share the array: calls that
  * overlap on the GPU (from several streams or threads at once) race and give
  * wrong results; serialise them.  The array keeps the last call's contents, and
  * each call clears the part it uses before reducing.

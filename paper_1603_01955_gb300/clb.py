@@ -99,6 +99,8 @@ def _load():
                                      C.POINTER(P)]
     lib.clb_batch_step.argtypes = [P, C.c_int64]
     lib.clb_batch_tune.argtypes = [P, I]
+    lib.clb_batch_set_schedule.argtypes = [P, C.c_int, C.c_int]
+    lib.clb_batch_schedule.argtypes = [P, I, I, I, I]
     lib.clb_batch_observables.argtypes = [P, C.POINTER(clb_scalars)]
     lib.clb_batch_get_state.argtypes = [P, C.c_int, P]
     lib.clb_batch_set_state.argtypes = [P, C.c_int, P]
@@ -107,14 +109,18 @@ def _load():
     lib.clb_adjoint_forward.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double,
                                         C.c_int64, C.c_int, C.POINTER(clb_opts), C.POINTER(P), D]
     lib.clb_adjoint_backward.argtypes = [P, C.c_double, D]
+    lib.clb_adjoint_q.argtypes = [P, D]
+    lib.clb_adjoint_q_backward.argtypes = [P, C.c_double, D]
     lib.clb_adjoint_destroy.argtypes = [P]
     lib.clb_peak_fma.argtypes = [C.c_int, P, D]
     for name in ("clb_create", "clb_step", "clb_observables", "clb_get_state", "clb_set_state",
                  "clb_info", "clb_sync", "clb_destroy", "clb_save", "clb_load", "clb_observables_noalloc",
                  "clb_batch_create",
-                 "clb_batch_step", "clb_batch_tune", "clb_batch_observables", "clb_batch_get_state",
+                 "clb_batch_step", "clb_batch_tune", "clb_batch_set_schedule", "clb_batch_schedule",
+                 "clb_batch_observables", "clb_batch_get_state",
                  "clb_batch_set_state", "clb_batch_info", "clb_batch_destroy", "clb_adjoint_forward",
-                 "clb_adjoint_backward", "clb_adjoint_destroy", "clb_peak_fma"):
+                 "clb_adjoint_backward", "clb_adjoint_q", "clb_adjoint_q_backward", "clb_adjoint_destroy",
+                 "clb_peak_fma"):
         getattr(lib, name).restype = C.c_int
     return lib
 
@@ -361,6 +367,16 @@ def clb_batch_tune(b):
     return blk.value
 
 
+def clb_batch_set_schedule(b, nodes_per_thread, packed):
+    return _check(lib.clb_batch_set_schedule(b, int(nodes_per_thread), int(packed)))
+
+
+def clb_batch_schedule(b):
+    v = [C.c_int() for _ in range(4)]
+    _check(lib.clb_batch_schedule(b, *[C.byref(x) for x in v]))
+    return dict(zip(("threads_per_block", "nodes_per_thread", "blocks", "packed"), (x.value for x in v)))
+
+
 def clb_batch_observables(b, n):
     s = (clb_scalars * n)()
     _check(lib.clb_batch_observables(b, s))
@@ -441,6 +457,12 @@ class Batch:
     def tune(self):
         return clb_batch_tune(self.b)
 
+    def set_schedule(self, nodes_per_thread, packed):
+        clb_batch_set_schedule(self.b, nodes_per_thread, packed)
+
+    def schedule(self):
+        return clb_batch_schedule(self.b)
+
     def info(self):
         blk, step, _ = clb_batch_info(self.b)
         return {"block_x": blk, "step": step}
@@ -476,14 +498,26 @@ def clb_adjoint_backward(h, seed=1.0):
     return list(grad)
 
 
+def clb_adjoint_q(h):
+    q = C.c_double()
+    _check(lib.clb_adjoint_q(h, C.byref(q)))
+    return q.value
+
+
+def clb_adjoint_q_backward(h, seed=1.0):
+    grad = (C.c_double * 3)()
+    _check(lib.clb_adjoint_q_backward(h, float(seed), grad))
+    return list(grad)
+
+
 def clb_adjoint_destroy(h):
     return _check(lib.clb_adjoint_destroy(h))
 
 
 class FlowGradient:
     """J = mean_x sum_y u_x of a periodic body-force channel after nsteps, and
-    its adjoint gradient with respect to (r_b, a, G).  Q = J / (3 G ny^2
-    sqrt(1/6)) is the normalised flow rate of Sec. 3.1."""
+    its adjoint gradient with respect to (r_b, a, G); the normalised flow rate
+    Q of Sec. 3.1 and its gradient come from the library as well."""
 
     def __init__(self, nx, ny, kn, a, r, g, nsteps, storage="fp32s", checkpoint_every=0, b2=0.55, sigma=1.0,
                  s3=1.1, s8=1.2, rho_out=1.0, stream=None):
@@ -509,7 +543,6 @@ class FlowGradient:
 
         self._hooks = (ALLOC_FN(_alloc), FREE_FN(_free))
         o.alloc, o.free = self._hooks
-        self.ny, self.g = int(ny), float(g)
         self.h, self.J = clb_adjoint_forward(nx, ny, kn, a, r, g, nsteps, checkpoint_every, o)
 
     def grad(self, seed=1.0):
@@ -518,7 +551,12 @@ class FlowGradient:
 
     @property
     def q_norm(self):
-        return self.J / (3.0 * self.g * self.ny**2 * (1.0 / 6.0) ** 0.5)
+        """Q after the forward pass (clb_adjoint_q)."""
+        return clb_adjoint_q(self.h)
+
+    def q_grad(self, seed=1.0):
+        """seed * dQ/d(r_b, a, G) (clb_adjoint_q_backward)."""
+        return clb_adjoint_q_backward(self.h, seed)
 
     def close(self):
         if getattr(self, "h", None):
@@ -545,18 +583,13 @@ def _flow_rate_function():
             fg = FlowGradient(cfg["nx"], cfg["ny"], cfg["kn"], float(a), float(r), float(g), cfg["nsteps"],
                               storage=cfg.get("storage", "fp32s"), checkpoint_every=cfg.get("checkpoint_every", 0))
             ctx.fg = fg
-            ctx.norm = 3.0 * float(g) * cfg["ny"] ** 2 * (1.0 / 6.0) ** 0.5
-            ctx.g = float(g)
-            return torch.tensor(fg.J / ctx.norm, dtype=torch.float64)
+            return torch.tensor(fg.q_norm, dtype=torch.float64)
 
         @staticmethod
         def backward(ctx, gout):
             fg = ctx.fg
-            dr, da, dg = fg.grad(1.0)
-            q = fg.J / ctx.norm
+            grads = fg.q_grad(float(gout))
             fg.close()
-            s = float(gout)
-            grads = (dr / ctx.norm * s, da / ctx.norm * s, (dg / ctx.norm - q / ctx.g) * s)
             return tuple(torch.tensor(v, dtype=torch.float64) for v in grads) + (None,)
 
     return FlowRate

@@ -145,7 +145,10 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 constexpr int kAdjThreads = 128;
 
 // mu = J_C^T lambda_{t+1} at every node (indexed like the pre-collision
-// populations), and the parameter terms of step t into acc[0..2] (r, a, G).
+// populations), and the parameter terms of step t added to this block's slots
+// acc[k * gridDim.x + blockIdx.x], k = 0, 1, 2 (r, a, G).  Each slot has one
+// writer and the launches run in stream order, so every slot is summed in a
+// fixed order and the gradient is the same bit for bit on every run.
 template <class R>
 __global__ void __launch_bounds__(kAdjThreads)
     adj_back_kernel(const R* f_t, const R* lam, R* mu, double* acc, AdjConst<R> k) {
@@ -194,9 +197,9 @@ __global__ void __launch_bounds__(kAdjThreads)
     ga = block_sum(ga, sh);
     gg = block_sum(gg, sh);
     if (threadIdx.x == 0) {
-        atomicAdd(acc + 0, gr);
-        atomicAdd(acc + 1, ga);
-        atomicAdd(acc + 2, gg);
+        acc[0 * gridDim.x + blockIdx.x] += gr;
+        acc[1 * gridDim.x + blockIdx.x] += ga;
+        acc[2 * gridDim.x + blockIdx.x] += gg;
     }
 }
 
@@ -262,7 +265,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_final_kernel(const R* f, R* l
         }
     }
     js = block_sum(js, sh);
-    if (threadIdx.x == 0) atomicAdd(acc + 3, js);
+    if (threadIdx.x == 0) acc[3 * gridDim.x + blockIdx.x] = js;
 }
 
 }  // namespace
@@ -278,7 +281,8 @@ struct clb_adjoint {
     void* lam[2] = {nullptr, nullptr};
     void* lam_final = nullptr;  // lambda_N = dJ/df_N, kept for every backward call
     void* mu = nullptr;
-    double* acc = nullptr; // r, a, G sums and J
+    double* acc = nullptr; // per-block partial sums [4][nb]: r, a, G and J
+    int nb = 0;            // blocks of every adjoint launch
     AdjConst<float> kf;
     AdjConst<double> kd;
     double J = 0;
@@ -319,10 +323,24 @@ template <class R> R* state_at(void* base, size_t state_elems, int64_t k) {
     return static_cast<R*>(base) + (size_t)k * state_elems;
 }
 
+// Copy the [4][nb] partial sums to the host and add each row in block order.
+cudaError_t sum_partials(clb_adjoint* h, int rows, double* out) {
+    std::vector<double> part((size_t)rows * h->nb);
+    cudaError_t e = cudaMemcpyAsync(part.data(), h->acc, part.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                    h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return e;
+    for (int k = 0; k < rows; ++k) {
+        double v = 0;
+        for (int b = 0; b < h->nb; ++b) v += part[(size_t)k * h->nb + b];
+        out[k] = v;
+    }
+    return cudaSuccess;
+}
+
 template <class R> cudaError_t forward_run(clb_adjoint* h) {
     const AdjConst<R>& k = kconst<R>(h);
-    const size_t nn = (size_t)h->nx * h->ny;
-    const int nb = blocks_for(nn, kAdjThreads);
+    const int nb = h->nb;
     R* cur = state_at<R>(h->seg, h->state_elems, 0);
     R* nxt = state_at<R>(h->seg, h->state_elems, 1);
     cudaError_t e = cudaMemsetAsync(cur, 0, h->state_elems * sizeof(R), h->stream);  // f^eq(rho_out, 0)
@@ -336,24 +354,22 @@ template <class R> cudaError_t forward_run(clb_adjoint* h) {
         std::swap(cur, nxt);
     }
     if (e != cudaSuccess) return e;
-    // final state and J, lambda_N (into lam[0])
-    e = cudaMemsetAsync(h->acc, 0, 4 * sizeof(double), h->stream);
+    // final state and J, lambda_N (into lam_final)
+    e = cudaMemsetAsync(h->acc, 0, (size_t)4 * nb * sizeof(double), h->stream);
     if (e == cudaSuccess) {
         adj_final_kernel<R><<<nb, kAdjThreads, 0, h->stream>>>(cur, static_cast<R*>(h->lam_final), h->acc, k);
         e = cudaGetLastError();
     }
     double hacc[4];
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hacc, h->acc, sizeof hacc, cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess) e = sum_partials(h, 4, hacc);
     if (e == cudaSuccess) h->J = hacc[3];
     return e;
 }
 
 template <class R> cudaError_t backward_run(clb_adjoint* h, double seed, double grad[3]) {
     const AdjConst<R>& k = kconst<R>(h);
-    const size_t nn = (size_t)h->nx * h->ny;
-    const int nb = blocks_for(nn, kAdjThreads);
-    cudaError_t e = cudaMemsetAsync(h->acc, 0, 3 * sizeof(double), h->stream);
+    const int nb = h->nb;
+    cudaError_t e = cudaMemsetAsync(h->acc, 0, (size_t)3 * nb * sizeof(double), h->stream);
     R* lam = static_cast<R*>(h->lam[0]);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(lam, h->lam_final, h->state_elems * sizeof(R), cudaMemcpyDeviceToDevice, h->stream);
@@ -381,8 +397,7 @@ template <class R> cudaError_t backward_run(clb_adjoint* h, double seed, double 
         }
     }
     double hacc[3];
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hacc, h->acc, sizeof hacc, cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess) e = sum_partials(h, 3, hacc);
     if (e != cudaSuccess) return e;
     // explicit dependence of J on G: u_x = sum e f / rho - G/2, summed over y
     grad[0] = seed * hacc[0];
@@ -486,7 +501,8 @@ clb_status clb_adjoint_forward(int nx, int ny, double kn, double a, double r, do
     h->lam[1] = h->dalloc(sb);
     h->lam_final = h->dalloc(sb);
     h->mu = h->dalloc(sb);
-    h->acc = static_cast<double*>(h->dalloc(4 * sizeof(double)));
+    h->nb = blocks_for((size_t)nx * ny, kAdjThreads);
+    h->acc = static_cast<double*>(h->dalloc((size_t)4 * h->nb * sizeof(double)));
     if (!h->ckpt || !h->seg || !h->lam[0] || !h->lam[1] || !h->lam_final || !h->mu || !h->acc) {
         clb_adjoint_destroy(h);
         return (clb_status)set_error(CLB_ENOMEM, "clb_adjoint_forward: device allocation failed");
@@ -506,6 +522,32 @@ clb_status clb_adjoint_backward(clb_adjoint* h, double seed, double grad[3]) {
     if (!h || !grad) return (clb_status)set_error(CLB_EINVAL, "clb_adjoint_backward: NULL argument");
     cudaError_t e = h->storage == CLB_FP64 ? backward_run<double>(h, seed, grad) : backward_run<float>(h, seed, grad);
     if (e != cudaSuccess) return (clb_status)set_error(CLB_ECUDA, "clb_adjoint_backward: %s", cudaGetErrorString(e));
+    return CLB_OK;
+}
+
+// Q = J / (3 G ny^2 sqrt(1/6)): the normalised flow rate of Sec. 3.1 with
+// RT = 1/3, p = rho0 RT and F = rho0 G.
+static double q_norm_of(const clb_adjoint* h) { return 3.0 * h->g * (double)h->ny * h->ny * std::sqrt(1.0 / 6.0); }
+
+clb_status clb_adjoint_q(const clb_adjoint* h, double* q) {
+    if (!h || !q) return (clb_status)set_error(CLB_EINVAL, "clb_adjoint_q: NULL argument");
+    if (h->g == 0) return (clb_status)set_error(CLB_EINVAL, "clb_adjoint_q: Q is undefined for G = 0");
+    *q = h->J / q_norm_of(h);
+    return CLB_OK;
+}
+
+clb_status clb_adjoint_q_backward(clb_adjoint* h, double seed, double grad[3]) {
+    clb::TraceRange trace_("clb_adjoint_q_backward");
+    if (!h || !grad) return (clb_status)set_error(CLB_EINVAL, "clb_adjoint_q_backward: NULL argument");
+    if (h->g == 0) return (clb_status)set_error(CLB_EINVAL, "clb_adjoint_q_backward: Q is undefined for G = 0");
+    double dj[3];
+    cudaError_t e = h->storage == CLB_FP64 ? backward_run<double>(h, 1.0, dj) : backward_run<float>(h, 1.0, dj);
+    if (e != cudaSuccess) return (clb_status)set_error(CLB_ECUDA, "clb_adjoint_q_backward: %s", cudaGetErrorString(e));
+    // dQ/dtheta = (dJ/dtheta) / norm, and for G also the normalisation's own -Q/G
+    const double norm = q_norm_of(h), q = h->J / norm;
+    grad[0] = seed * (dj[0] / norm);
+    grad[1] = seed * (dj[1] / norm);
+    grad[2] = seed * (dj[2] / norm - q / h->g);
     return CLB_OK;
 }
 

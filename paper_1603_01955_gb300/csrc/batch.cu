@@ -8,9 +8,15 @@
 // barrier, collide (Eq. 4, 6-13 with the channel's own s_v, s_q from Eq. 18,
 // 21) and write back in place, barrier.  Global memory is touched once at
 // the start and once at the end of a launch.  The host replays a CUDA graph
-// holding one such launch of a fixed number of steps; an autotuner picks the
-// block size (and with it the nodes per thread) by timing the candidates on a
-// copy of the state.
+// holding one such launch of a fixed number of steps.
+//
+// Schedule: each channel is updated by a warp-aligned range of a block's
+// threads, each thread taking `npt` nodes (1, 2, 4 or 8).  Unpacked, every
+// channel has a block of its own; packed, small channels share a block (each
+// on its own thread range and shared-memory region, all behind the same block
+// barriers), which cuts the blocks of a sweep with many small channels.  An
+// autotuner times every feasible (npt, packed) pair on a copy of the state
+// and keeps the fastest.  Every schedule computes the same bits.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -33,11 +39,25 @@ struct BatchChannel {
     long long offset;  // element offset of the channel's [9][ny][nx] block
 };
 
+// Where a channel runs under a schedule: threads [t0, t0 + threads) of its
+// block, its copy (copies) in the block's shared memory from element smem_off.
+struct BatchSlot {
+    int t0, threads, smem_off, block;
+};
+
 struct BatchArgs {
     void* state;
     const BatchChannel* ch;
     const KC<float>* kf;   // per-channel constants
     const KC<double>* kd;
+};
+
+// A schedule's device tables: per block, the first entry and the count of its
+// channels in `order`; per channel, its slot.
+struct SchedArgs {
+    const int2* groups;
+    const int* order;
+    const BatchSlot* slots;
 };
 
 template <typename R> __device__ __forceinline__ const KC<R>* kcs(const BatchArgs& a);
@@ -141,15 +161,32 @@ __device__ __forceinline__ void gather_at(const R* s, const Pull& p, R r, R rc, 
 }
 
 template <class T, int NPT>
-__global__ void __launch_bounds__(512) batch_kernel(const BatchArgs a, int nsteps, int two_buffers) {
+__global__ void __launch_bounds__(512) batch_kernel(const BatchArgs a, const SchedArgs sc, int nsteps, int two_buffers) {
     using R = T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    R* s = reinterpret_cast<R*>(smem_raw);
-    const BatchChannel ch = a.ch[blockIdx.x];
-    const KC<R> c = kcs<R>(a)[blockIdx.x];
+    // this thread's channel: the block's channel whose thread range holds it
+    // (none for the padding threads, which only take part in the barriers)
+    const int2 gr = sc.groups[blockIdx.x];
+    int k = -1;
+    BatchSlot sl{0, 1, 0, 0};
+    for (int j = 0; j < gr.y; ++j) {
+        const int kk = sc.order[gr.x + j];
+        const BatchSlot q = sc.slots[kk];
+        if ((int)threadIdx.x >= q.t0 && (int)threadIdx.x < q.t0 + q.threads) {
+            k = kk;
+            sl = q;
+        }
+    }
+    const bool mine = k >= 0;
+    const BatchChannel ch = mine ? a.ch[k] : BatchChannel{1, 1, 0};
+    KC<R> c{};
+    if (mine) c = kcs<R>(a)[k];
     const int nx = ch.nx, ny = ch.ny, nn = nx * ny;
+    const int lt = (int)threadIdx.x - sl.t0, nth = sl.threads;  // thread within the channel's range
+    R* s = reinterpret_cast<R*>(smem_raw) + sl.smem_off;
     T* g = static_cast<T*>(a.state) + ch.offset;
-    for (int k = threadIdx.x; k < 9 * nn; k += blockDim.x) s[k] = g[k];
+    if (mine)
+        for (int e = lt; e < 9 * nn; e += nth) s[e] = g[e];
     const R r = c.r, rc = c.rc, ref = c.ref0;
     __syncthreads();
     R* out = two_buffers ? s + 9 * nn : s;
@@ -159,7 +196,7 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchArgs a, int nstep
     if constexpr (kPre) {
 #pragma unroll
         for (int q = 0; q < NPT; ++q) {
-            const int node = threadIdx.x + q * blockDim.x;
+            const int node = lt + q * nth;
             pl[q] = pull_of(nx, ny, node % nx, node / nx);
         }
     }
@@ -167,8 +204,8 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchArgs a, int nstep
         R f[NPT][9];
 #pragma unroll
         for (int q = 0; q < NPT; ++q) {
-            const int node = threadIdx.x + q * blockDim.x;
-            if (node < nn) {
+            const int node = lt + q * nth;
+            if (mine && node < nn) {
                 if constexpr (kPre)
                     gather_at(s, pl[q], r, rc, f[q]);
                 else
@@ -176,35 +213,37 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchArgs a, int nstep
             }
         }
         if (!two_buffers) __syncthreads();
-        if constexpr (std::is_same<R, float>::value && NPT % 2 == 0) {
-            // two nodes per packed FP32 instruction (bit for bit the one-node collision)
+        if (mine) {
+            if constexpr (std::is_same<R, float>::value && NPT % 2 == 0) {
+                // two nodes per packed FP32 instruction (bit for bit the one-node collision)
 #pragma unroll
-            for (int q = 0; q < NPT; q += 2) {
-                const int n0 = threadIdx.x + q * blockDim.x, n1 = n0 + blockDim.x;
-                if (n1 < nn) {
-                    float2 d[9];
+                for (int q = 0; q < NPT; q += 2) {
+                    const int n0 = lt + q * nth, n1 = n0 + nth;
+                    if (n1 < nn) {
+                        float2 d[9];
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) d[i] = make_float2(f[q][i], f[q + 1][i]);
-                    collide<R, MODE_PERIODIC, float2>(d, ln::bc<float2>(ref), c);
+                        for (int i = 0; i < 9; ++i) d[i] = make_float2(f[q][i], f[q + 1][i]);
+                        collide<R, MODE_PERIODIC, float2>(d, ln::bc<float2>(ref), c);
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) {
-                        out[i * nn + n0] = d[i].x;
-                        out[i * nn + n1] = d[i].y;
+                        for (int i = 0; i < 9; ++i) {
+                            out[i * nn + n0] = d[i].x;
+                            out[i * nn + n1] = d[i].y;
+                        }
+                    } else if (n0 < nn) {
+                        collide<R, MODE_PERIODIC>(f[q], ref, c);
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) out[i * nn + n0] = f[q][i];
                     }
-                } else if (n0 < nn) {
-                    collide<R, MODE_PERIODIC>(f[q], ref, c);
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) out[i * nn + n0] = f[q][i];
                 }
-            }
-        } else {
+            } else {
 #pragma unroll
-            for (int q = 0; q < NPT; ++q) {
-                const int node = threadIdx.x + q * blockDim.x;
-                if (node < nn) {
-                    collide<R, MODE_PERIODIC>(f[q], ref, c);
+                for (int q = 0; q < NPT; ++q) {
+                    const int node = lt + q * nth;
+                    if (node < nn) {
+                        collide<R, MODE_PERIODIC>(f[q], ref, c);
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) out[i * nn + node] = f[q][i];
+                        for (int i = 0; i < 9; ++i) out[i * nn + node] = f[q][i];
+                    }
                 }
             }
         }
@@ -215,7 +254,8 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchArgs a, int nstep
             out = t2;
         }
     }
-    for (int k = threadIdx.x; k < 9 * nn; k += blockDim.x) g[k] = s[k];
+    if (mine)
+        for (int e = lt; e < 9 * nn; e += nth) g[e] = s[e];
 }
 
 // Per channel: mass flow (mean over x of sum_y rho u_x), sum of u_x (for Q),
@@ -282,14 +322,24 @@ __global__ void batch_canon_kernel(void* state, long long offset, long long n, d
 
 }  // namespace
 
+// A schedule (see the file comment) with its device tables.
+struct BatchSched {
+    int npt = 0, packed = 0;
+    int block = 0;        // threads per block
+    int nblocks = 0;
+    int two_buffers = 0;  // every channel keeps two copies in shared memory
+    size_t smem = 0;      // bytes of shared memory per block (the largest group)
+    void* mem = nullptr;  // one device allocation: groups, order, slots
+    SchedArgs args{};
+};
+
 struct clb_batch {
     int n = 0, storage = 0, block_x = 0;
     bool tuned = false;
     size_t elem = 0;
     long long total = 0;  // elements of the state
-    size_t smem = 0;      // bytes of shared memory per block
-    int two_buffers = 0;  // the block keeps two copies of its channel (when they fit)
     int max_nodes = 0;
+    BatchSched sched;     // the schedule in use
     std::vector<BatchChannel> hch;
     std::vector<double> kn;
     std::vector<int> nx, ny;
@@ -303,7 +353,7 @@ struct clb_batch {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cudaGraphExec_t graph = nullptr;
-    int graph_steps = 0, graph_block = 0;
+    int graph_steps = 0;
     void* (*alloc)(size_t, void*) = nullptr;
     void (*dealloc)(void*, void*) = nullptr;
     void* alloc_ctx = nullptr;
@@ -329,31 +379,81 @@ struct clb_batch {
 namespace {
 
 constexpr int kGraphSteps = 500;  // time steps per persistent launch in the replayed graph
+constexpr size_t kSmemCap = 200 * 1024;  // shared memory a block may take
+constexpr int kPackedBlock = 256;        // threads per block of a packed schedule
 
-int npt_for(int max_nodes, int block) { return (max_nodes + block - 1) / block; }
-
-template <class T>
-cudaError_t launch_batch(clb_batch* b, void* state, int block, int nsteps, cudaStream_t st) {
-    BatchArgs a{state, b->dch, b->dkf, b->dkd};
-    const int npt = npt_for(b->max_nodes, block);
-    dim3 grid(b->n), blk(block);
-    switch (npt) {
-        case 1: batch_kernel<T, 1><<<grid, blk, b->smem, st>>>(a, nsteps, b->two_buffers); break;
-        case 2: batch_kernel<T, 2><<<grid, blk, b->smem, st>>>(a, nsteps, b->two_buffers); break;
-        case 3:
-        case 4: batch_kernel<T, 4><<<grid, blk, b->smem, st>>>(a, nsteps, b->two_buffers); break;
-        case 5:
-        case 6:
-        case 7:
-        case 8: batch_kernel<T, 8><<<grid, blk, b->smem, st>>>(a, nsteps, b->two_buffers); break;
-        default: return cudaErrorInvalidConfiguration;
-    }
-    return cudaGetLastError();
+void free_sched(clb_batch* b, BatchSched& sc) {
+    b->dfree(sc.mem);
+    sc = BatchSched{};
 }
 
-cudaError_t launch(clb_batch* b, void* state, int block, int nsteps, cudaStream_t st) {
-    return b->storage == CLB_FP64 ? launch_batch<double>(b, state, block, nsteps, st)
-                                  : launch_batch<float>(b, state, block, nsteps, st);
+// Build schedule (npt, packed): per channel ceil(nodes / npt) threads rounded
+// up to whole warps; unpacked, one channel per block, blocks as wide as the
+// widest channel; packed, blocks of kPackedBlock threads (or the widest
+// channel, if wider), filled first-fit with the channels by decreasing width,
+// each block within kSmemCap bytes.  Two copies per
+// channel when every block's channels still fit.  Returns false (no device
+// work) if the schedule is not feasible.
+bool plan_sched(const clb_batch* b, int npt, int packed, int block_min, BatchSched& sc, std::vector<int2>& groups,
+                std::vector<int>& order, std::vector<BatchSlot>& slots) {
+    const int n = b->n;
+    std::vector<int> width(n);
+    int block = block_min, total = 0;
+    for (int k = 0; k < n; ++k) {
+        const int nodes = b->nx[k] * b->ny[k];
+        width[k] = ((nodes + npt - 1) / npt + 31) / 32 * 32;
+        block = std::max(block, width[k]);
+        total += width[k];
+    }
+    if (block > 512) return false;
+    if (packed) block = std::max(block, std::min(kPackedBlock, total));
+    const size_t one = 9 * b->elem;  // bytes per node and copy
+    int two = 2 * one * b->max_nodes <= kSmemCap;
+    std::vector<int> idx(n);
+    for (int k = 0; k < n; ++k) idx[k] = k;
+    if (packed) std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return width[x] > width[y]; });
+    for (;;) {
+        groups.clear();
+        order.clear();
+        slots.assign(n, BatchSlot{0, 0, 0, 0});
+        std::vector<int> used_t, used_m;  // per block: threads and shared-memory elements taken
+        std::vector<std::vector<int>> members;
+        for (int k : idx) {
+            const int elems = ((two ? 2 : 1) * 9 * b->nx[k] * b->ny[k] + 3) / 4 * 4;  // 16-byte aligned regions
+            int blk = -1;
+            if (packed)
+                for (size_t j = 0; j < used_t.size() && blk < 0; ++j)
+                    if (used_t[j] + width[k] <= block && (used_m[j] + elems) * b->elem <= kSmemCap) blk = (int)j;
+            if (blk < 0) {
+                blk = (int)used_t.size();
+                used_t.push_back(0);
+                used_m.push_back(0);
+                members.emplace_back();
+            }
+            slots[k] = BatchSlot{used_t[blk], width[k], used_m[blk], blk};
+            used_t[blk] += width[k];
+            used_m[blk] += elems;
+            members[blk].push_back(k);
+        }
+        size_t smem = 0;
+        for (size_t j = 0; j < members.size(); ++j) {
+            groups.push_back(make_int2((int)order.size(), (int)members[j].size()));
+            for (int k : members[j]) order.push_back(k);
+            smem = std::max(smem, used_m[j] * b->elem);
+        }
+        if (smem > kSmemCap) {
+            if (!two) return false;
+            two = 0;  // retry with one copy per channel
+            continue;
+        }
+        sc.npt = npt;
+        sc.packed = packed;
+        sc.block = block;
+        sc.nblocks = (int)groups.size();
+        sc.two_buffers = two;
+        sc.smem = std::max<size_t>(smem, 16);
+        return true;
+    }
 }
 
 template <class T> cudaError_t set_smem_limit(size_t bytes) {
@@ -367,6 +467,55 @@ template <class T> cudaError_t set_smem_limit(size_t bytes) {
     return e;
 }
 
+// Plan and upload schedule (npt, packed); CLB_EINVAL if it is not feasible.
+clb_status make_sched(clb_batch* b, int npt, int packed, int block_min, BatchSched& sc) {
+    std::vector<int2> groups;
+    std::vector<int> order;
+    std::vector<BatchSlot> slots;
+    BatchSched t;
+    if (!plan_sched(b, npt, packed, block_min, t, groups, order, slots))
+        return (clb_status)set_error(CLB_EINVAL, "clb_batch: schedule (%d nodes per thread, packed %d) does not fit",
+                                     npt, packed);
+    const size_t bg = groups.size() * sizeof(int2), bo = order.size() * sizeof(int), bs = slots.size() * sizeof(BatchSlot);
+    const size_t og = 0, oo = (bg + 15) / 16 * 16, os = oo + (bo + 15) / 16 * 16;
+    t.mem = b->dalloc(os + bs);
+    if (!t.mem) return (clb_status)set_error(CLB_ENOMEM, "clb_batch: device allocation of a schedule failed");
+    char* m = static_cast<char*>(t.mem);
+    cudaError_t e = cudaMemcpyAsync(m + og, groups.data(), bg, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(m + oo, order.data(), bo, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(m + os, slots.data(), bs, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = b->storage == CLB_FP64 ? set_smem_limit<double>(t.smem) : set_smem_limit<float>(t.smem);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // the host vectors go out of scope
+    if (e != cudaSuccess) {
+        b->dfree(t.mem);
+        return (clb_status)set_error(CLB_ECUDA, "clb_batch: schedule upload: %s", cudaGetErrorString(e));
+    }
+    t.args = SchedArgs{reinterpret_cast<const int2*>(m + og), reinterpret_cast<const int*>(m + oo),
+                       reinterpret_cast<const BatchSlot*>(m + os)};
+    sc = t;
+    return CLB_OK;
+}
+
+template <class T>
+cudaError_t launch_batch(clb_batch* b, const BatchSched& sc, void* state, int nsteps, cudaStream_t st) {
+    BatchArgs a{state, b->dch, b->dkf, b->dkd};
+    dim3 grid(sc.nblocks), blk(sc.block);
+    switch (sc.npt) {
+        case 1: batch_kernel<T, 1><<<grid, blk, sc.smem, st>>>(a, sc.args, nsteps, sc.two_buffers); break;
+        case 2: batch_kernel<T, 2><<<grid, blk, sc.smem, st>>>(a, sc.args, nsteps, sc.two_buffers); break;
+        case 4: batch_kernel<T, 4><<<grid, blk, sc.smem, st>>>(a, sc.args, nsteps, sc.two_buffers); break;
+        case 8: batch_kernel<T, 8><<<grid, blk, sc.smem, st>>>(a, sc.args, nsteps, sc.two_buffers); break;
+        default: return cudaErrorInvalidConfiguration;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch(clb_batch* b, const BatchSched& sc, void* state, int nsteps, cudaStream_t st) {
+    return b->storage == CLB_FP64 ? launch_batch<double>(b, sc, state, nsteps, st)
+                                  : launch_batch<float>(b, sc, state, nsteps, st);
+}
+
 void drop_graph(clb_batch* b) {
     if (b->graph) cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
@@ -377,7 +526,7 @@ clb_status build_graph(clb_batch* b) {
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        cudaError_t le = launch(b, b->state, b->block_x, kGraphSteps, b->stream);
+        cudaError_t le = launch(b, b->sched, b->state, kGraphSteps, b->stream);
         e = cudaStreamEndCapture(b->stream, &g);
         if (e == cudaSuccess) e = le;
     }
@@ -388,8 +537,16 @@ clb_status build_graph(clb_batch* b) {
         return (clb_status)set_error(CLB_ECUDA, "clb_batch: graph capture: %s", cudaGetErrorString(e));
     }
     b->graph_steps = kGraphSteps;
-    b->graph_block = b->block_x;
     return CLB_OK;
+}
+
+// Make `sc` the schedule in use (the old one is released, the graph rebuilt on demand).
+void adopt_sched(clb_batch* b, BatchSched& sc) {
+    drop_graph(b);
+    free_sched(b, b->sched);
+    b->sched = sc;
+    sc = BatchSched{};
+    b->block_x = b->sched.block;
 }
 
 }  // namespace
@@ -400,6 +557,7 @@ clb_status clb_batch_destroy(clb_batch* b) {
     if (!b) return CLB_OK;
     if (b->stream) cudaStreamSynchronize(b->stream);
     drop_graph(b);
+    free_sched(b, b->sched);
     b->dfree(b->state);
     b->dfree(b->dch);
     b->dfree(b->dkf);
@@ -446,8 +604,6 @@ clb_status clb_batch_create(int n, const int* nx, const int* ny, const double* k
     b->n = n;
     b->storage = o.storage;
     b->elem = elem;
-    b->two_buffers = 2 * smem <= 200 * 1024;
-    b->smem = b->two_buffers ? 2 * smem : smem;
     b->max_nodes = max_nodes;
     b->alloc = o.alloc;
     b->dealloc = o.free;
@@ -456,7 +612,6 @@ clb_status clb_batch_create(int n, const int* nx, const int* ny, const double* k
     b->rho0 = o.rho_out;
     b->ref0 = o.storage == CLB_FP64 ? 0.0 : o.rho_out;
     b->r = r >= 0 ? r : r_from_sigma(o.sigma);
-    b->block_x = o.block_x ? o.block_x : std::min(512, ((max_nodes + 31) / 32) * 32);
     b->tuned = o.block_x != 0;
     long long off = 0;
     std::vector<KC<float>> kf(n);
@@ -505,11 +660,25 @@ clb_status clb_batch_create(int n, const int* nx, const int* ny, const double* k
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->dkd, kd.data(), n * sizeof(KC<double>), cudaMemcpyHostToDevice, b->stream);
     // initial state f^eq(rho_out, 0) = w_i rho_out: zero deviations (FP32) or w_i rho_out (FP64)
     if (e == cudaSuccess) e = cudaMemsetAsync(b->state, 0, b->total * elem, b->stream);
-    if (e == cudaSuccess) e = b->storage == CLB_FP64 ? set_smem_limit<double>(b->smem) : set_smem_limit<float>(b->smem);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) {
         clb_batch_destroy(b);
         return (clb_status)set_error(CLB_ECUDA, "clb_batch_create: %s", cudaGetErrorString(e));
+    }
+    {
+        // first schedule: opts.block_x threads per block, one channel per
+        // block (fixed); or one node per thread where that fits (tuned on
+        // first use)
+        const int want = o.block_x ? o.block_x : 512;
+        int npt = 1;
+        while (npt < 8 && (max_nodes + npt - 1) / npt > want) npt *= 2;
+        BatchSched sc;
+        clb_status st = make_sched(b, npt, 0, o.block_x, sc);
+        if (st != CLB_OK) {
+            clb_batch_destroy(b);
+            return st;
+        }
+        adopt_sched(b, sc);
     }
     if (b->storage == CLB_FP64) {
         const double w[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
@@ -533,40 +702,83 @@ clb_status clb_batch_create(int n, const int* nx, const int* ny, const double* k
 
 clb_status clb_batch_tune(clb_batch* b, int* block_out) {
     if (!b) return (clb_status)set_error(CLB_EINVAL, "clb_batch_tune: batch is NULL");
-    // time every block size on a scratch copy of the state (results do not
-    // depend on it, only the speed does)
+    // time every feasible schedule on a scratch copy of the state (results do
+    // not depend on the schedule, only the speed does)
     void* scratch = b->dalloc(b->total * b->elem);
     if (!scratch) return (clb_status)set_error(CLB_ENOMEM, "clb_batch_tune: device allocation failed");
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    int best_block = b->block_x;
+    BatchSched best_sc;
     cudaError_t err = cudaSuccess;
+    clb_status st = CLB_OK;
     const int trial_steps = 200;
-    for (int block = 64; block <= 512 && err == cudaSuccess; block *= 2) {
-        if (npt_for(b->max_nodes, block) > 8) continue;
-        err = cudaMemcpyAsync(scratch, b->state, b->total * b->elem, cudaMemcpyDeviceToDevice, b->stream);
-        if (err == cudaSuccess) err = launch(b, scratch, block, 20, b->stream);  // warm-up
-        if (err == cudaSuccess) err = cudaEventRecord(e0, b->stream);
-        if (err == cudaSuccess) err = launch(b, scratch, block, trial_steps, b->stream);
-        if (err == cudaSuccess) err = cudaEventRecord(e1, b->stream);
-        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
-        float ms = 0;
-        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
-        if (err == cudaSuccess && ms < best) {
-            best = ms;
-            best_block = block;
+    int unpacked_blocks = 0;
+    for (int npt = 1; npt <= 8 && err == cudaSuccess && st == CLB_OK; npt *= 2) {
+        for (int packed = 0; packed <= 1 && err == cudaSuccess; ++packed) {
+            BatchSched sc;
+            if (make_sched(b, npt, packed, 0, sc) != CLB_OK) {
+                set_error(CLB_OK, "%s", "");  // an infeasible schedule is not an error of the tuner
+                continue;
+            }
+            if (!packed) unpacked_blocks = sc.nblocks;
+            if (packed && sc.nblocks == unpacked_blocks) {  // nothing was packed: the same schedule
+                free_sched(b, sc);
+                continue;
+            }
+            err = cudaMemcpyAsync(scratch, b->state, b->total * b->elem, cudaMemcpyDeviceToDevice, b->stream);
+            if (err == cudaSuccess) err = launch(b, sc, scratch, 20, b->stream);  // warm-up
+            if (err == cudaSuccess) err = cudaEventRecord(e0, b->stream);
+            if (err == cudaSuccess) err = launch(b, sc, scratch, trial_steps, b->stream);
+            if (err == cudaSuccess) err = cudaEventRecord(e1, b->stream);
+            if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+            float ms = 0;
+            if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+            if (err == cudaSuccess && ms < best) {
+                best = ms;
+                free_sched(b, best_sc);
+                best_sc = sc;
+            } else {
+                free_sched(b, sc);
+            }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaStreamSynchronize(b->stream);
     b->dfree(scratch);
-    if (err != cudaSuccess) return (clb_status)set_error(CLB_ECUDA, "clb_batch_tune: %s", cudaGetErrorString(err));
-    b->block_x = best_block;
+    if (err != cudaSuccess || !best_sc.mem) {
+        free_sched(b, best_sc);
+        return (clb_status)set_error(CLB_ECUDA, "clb_batch_tune: %s",
+                                     err != cudaSuccess ? cudaGetErrorString(err) : "no schedule fits");
+    }
+    adopt_sched(b, best_sc);
     b->tuned = true;
-    if (block_out) *block_out = best_block;
+    if (block_out) *block_out = b->block_x;
+    return CLB_OK;
+}
+
+clb_status clb_batch_set_schedule(clb_batch* b, int nodes_per_thread, int packed) {
+    if (!b) return (clb_status)set_error(CLB_EINVAL, "clb_batch_set_schedule: batch is NULL");
+    if (nodes_per_thread != 1 && nodes_per_thread != 2 && nodes_per_thread != 4 && nodes_per_thread != 8)
+        return (clb_status)set_error(CLB_EINVAL, "clb_batch_set_schedule: nodes per thread must be 1, 2, 4 or 8");
+    cudaStreamSynchronize(b->stream);  // the old tables may be in use by queued launches
+    BatchSched sc;
+    clb_status st = make_sched(b, nodes_per_thread, packed ? 1 : 0, 0, sc);
+    if (st != CLB_OK) return st;
+    adopt_sched(b, sc);
+    b->tuned = true;
+    return CLB_OK;
+}
+
+clb_status clb_batch_schedule(const clb_batch* b, int* threads_per_block, int* nodes_per_thread, int* blocks,
+                              int* packed) {
+    if (!b) return (clb_status)set_error(CLB_EINVAL, "clb_batch_schedule: batch is NULL");
+    if (threads_per_block) *threads_per_block = b->sched.block;
+    if (nodes_per_thread) *nodes_per_thread = b->sched.npt;
+    if (blocks) *blocks = b->sched.nblocks;
+    if (packed) *packed = b->sched.packed;
     return CLB_OK;
 }
 
@@ -577,7 +789,7 @@ clb_status clb_batch_step(clb_batch* b, int64_t n) {
         clb_status st = clb_batch_tune(b, nullptr);
         if (st != CLB_OK) return st;
     }
-    if (n >= kGraphSteps && (!b->graph || b->graph_block != b->block_x)) {
+    if (n >= kGraphSteps && !b->graph) {
         clb_status st = build_graph(b);
         if (st != CLB_OK) return st;
     }
@@ -588,7 +800,7 @@ clb_status clb_batch_step(clb_batch* b, int64_t n) {
         left -= kGraphSteps;
     }
     if (left > 0) {
-        cudaError_t e = launch(b, b->state, b->block_x, (int)left, b->stream);
+        cudaError_t e = launch(b, b->sched, b->state, (int)left, b->stream);
         if (e != cudaSuccess) return (clb_status)set_error(CLB_ECUDA, "clb_batch_step: %s", cudaGetErrorString(e));
     }
     b->step += n;

@@ -75,7 +75,9 @@ struct clb_sim {
     size_t buf_bytes = 0;
     void* buf[2] = {nullptr, nullptr};
     int cur = 0;            // buffer holding the last completed step
-    double* obs = nullptr;  // device scratch of the observable reductions
+    double* obs = nullptr;  // device scratch of the observable reductions: L.total doubles, the
+                            // wait-status word's copy, the reduction's block counter
+    double* hobs = nullptr; // pinned host copy of the first L.total + 1
     unsigned* status = nullptr;  // error bits of bounded device waits
     int pipeline = 1;       // 1 direct loads, 2.. TMA-staged tile shapes
     int withhold_tile = -1; // testing: TMA tile withheld in the first launch
@@ -220,15 +222,47 @@ template <> struct RowSum<float> {
     __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
+// Fixed-order sum of the per-block partials part[4 b + k] (b < nblocks) into
+// part[0..3] by the threads of one block: thread t takes b = t, t + n, ...,
+// then a tree over the threads.  The order depends on nothing but the sizes.
+__device__ __forceinline__ void sum_partials_block(double* obs, const ObsLayout& L, double (*sh)[kObsRows * kObsCols]) {
+    const int t = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+    double acc[4] = {0, 0, 0, 0};
+    for (int b = t; b < L.nblocks; b += nt)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[k] += __ldcg(obs + L.part + 4 * b + k);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) sh[k][t] = acc[k];
+    __syncthreads();
+    for (int w = nt / 2; w > 0; w >>= 1) {
+        if (t < w)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) sh[k][t] += sh[k][t + w];
+        __syncthreads();
+    }
+    if (t == 0)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) obs[L.part + k] = sh[k][0];
+}
+
 // Per column: m(x) = sum_y rho u_x, centreline rho, sum_y u_x; the profiles at
 // one column; per block: partial sums of m, u_x, rho and a non-finite count.
 // Densities and velocities come from the post-collision populations of the
 // last step: the collision keeps rho and adds rho F to the momentum (Eq. 4, 9),
 // so rho u = sum_i e_i f~_i - rho F/2 is Eq. 13 at that time level.
-template <class T>
+// kSumU: also sum u_x over every node (the normalised flow rate Q of a
+// body-force channel needs it); otherwise u_x is formed only at the profile
+// column, and a node is counted non-finite when rho u or rho is.
+// done (optional): a counter that is 0 on entry; the last block to finish
+// then sums the partials (sum_partials_block), moves *status into
+// *status_out, clears it, and resets the counter, so that one launch does
+// the whole reduction.  Without it obs_final_kernel does the sum.
+template <class T, bool kSumU>
 __global__ void __launch_bounds__(kObsCols* kObsRows)
-    obs_kernel(const T* f, double* obs, ObsLayout L, int nx, int ny, int pitch, int xoff, long long plane,
-               double ref0, double ref_slope, double gx, double gy, int prof_col, double isc) {
+    obs_kernel(const T* __restrict__ f, double* __restrict__ obs, ObsLayout L, int nx, int ny, int pitch,
+               int xoff, long long plane,
+               double ref0, double ref_slope, double gx, double gy, int prof_col, double isc,
+               unsigned* done = nullptr, unsigned* status = nullptr, double* status_out = nullptr) {
     // Per node in the storage's compute type (FP32 for FP32/16-bit storage,
     // whose values carry FP32 or coarser rounding already; FP64 for FP64),
     // summed over the thread's rows in that type (compensated in FP32) and
@@ -236,16 +270,18 @@ __global__ void __launch_bounds__(kObsCols* kObsRows)
     // deviations, so the reference part is exact.  The mass flow needs no
     // division: rho u_x = sum_i e_ix f~_i - rho F_x / 2.
     using R = RT<T>;
-    __shared__ double sh[5][kObsRows][kObsCols];
+    __shared__ double sh[5][kObsRows * kObsCols];
+    __shared__ bool last;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int x = blockIdx.x * kObsCols + tx;
     double m = 0, us = 0, mass = 0, rc = 0, bad = 0;
     if (x < nx) {
         const double ref = ref0 + ref_slope * x;
         const R hgx = R(0.5 * gx), hgy = R(0.5 * gy);
+        const bool want_u = kSumU || x == prof_col;
         RowSum<R> sm, su, sd;
         int rows = 0, nbad = 0;
-#pragma unroll 2
+#pragma unroll 4
         for (int y = ty; y < ny; y += kObsRows) {
             const T* row = f + (long long)y * pitch + xoff + x;
             R v[9];
@@ -256,11 +292,19 @@ __global__ void __launch_bounds__(kObsCols* kObsRows)
             const R rho = R(ref) + drho;
             const R mx = (v[1] - v[3]) + (a57 + a86) - hgx * rho;  // rho u_x
             const R my = (v[2] - v[4]) + (a57 - a86) - hgy * rho;  // rho u_y
-            const R irho = rcp(rho);
-            const R ux = mx * irho, uy = my * irho;
-            if (!isfinite(rho) || !isfinite(ux) || !isfinite(uy)) ++nbad;
+            if (want_u) {
+                const R irho = rcp(rho);
+                const R ux = mx * irho, uy = my * irho;
+                if (!isfinite(rho) || !isfinite(ux) || !isfinite(uy)) ++nbad;
+                su.add(ux);
+                if (x == prof_col) {
+                    obs[L.prof_x + y] = (double)ux;
+                    obs[L.prof_y + y] = (double)uy;
+                }
+            } else if (!isfinite(rho) || !isfinite(mx) || !isfinite(my) || rho == R(0)) {
+                ++nbad;
+            }
             sm.add(mx);
-            su.add(ux);
             sd.add(drho);
             ++rows;
             // centreline: the middle row, or the mean of the two middle rows
@@ -269,30 +313,27 @@ __global__ void __launch_bounds__(kObsCols* kObsRows)
             } else if (y == ny / 2 - 1 || y == ny / 2) {
                 rc += 0.5 * (ref + (double)drho);
             }
-            if (x == prof_col) {
-                obs[L.prof_x + y] = (double)ux;
-                obs[L.prof_y + y] = (double)uy;
-            }
         }
         m = sm.value();
         us = su.value();
         mass = rows * ref + sd.value();
         bad = nbad;
     }
-    sh[0][ty][tx] = m;
-    sh[1][ty][tx] = us;
-    sh[2][ty][tx] = mass;
-    sh[3][ty][tx] = bad;
-    sh[4][ty][tx] = rc;
+    const int t = ty * kObsCols + tx;
+    sh[0][t] = m;
+    sh[1][t] = us;
+    sh[2][t] = mass;
+    sh[3][t] = bad;
+    sh[4][t] = rc;
     __syncthreads();
     if (ty == 0) {  // one full warp: column totals in a fixed order, then block partials
         double cm = 0, cu = 0, cmass = 0, cbad = 0, crc = 0;
         for (int k = 0; k < kObsRows; ++k) {
-            cm += sh[0][k][tx];
-            cu += sh[1][k][tx];
-            cmass += sh[2][k][tx];
-            cbad += sh[3][k][tx];
-            crc += sh[4][k][tx];
+            cm += sh[0][k * kObsCols + tx];
+            cu += sh[1][k * kObsCols + tx];
+            cmass += sh[2][k * kObsCols + tx];
+            cbad += sh[3][k * kObsCols + tx];
+            crc += sh[4][k * kObsCols + tx];
         }
         if (x < nx) {
             obs[L.m + x] = cm;
@@ -309,11 +350,34 @@ __global__ void __launch_bounds__(kObsCols* kObsRows)
             obs[L.part + 4 * blockIdx.x + 3] = cbad;
         }
     }
+    if (!done) return;
+    // the last block to finish sums every block's partials
+    __threadfence();
+    __syncthreads();
+    if (t == 0) last = atomicAdd(done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    sum_partials_block(obs, L, sh);
+    if (t == 0) {
+        if (status) {
+            *status_out = (double)*status;
+            *status = 0u;
+        }
+        *done = 0u;
+    }
 }
 
 // Sum the per-block partials in a fixed order (one warp), into part[0..3].
-__global__ void obs_final_kernel(double* obs, ObsLayout L) {
+// With a status word: also move it into *status_out and clear it, so that the
+// host reads the reductions and the error bits of the sweeps in one copy.
+__global__ void obs_final_kernel(double* obs, ObsLayout L, unsigned* status = nullptr,
+                                 double* status_out = nullptr) {
     const int t = threadIdx.x;
+    if (status && t == 0) {
+        *status_out = (double)*status;
+        *status = 0u;
+    }
     double acc[4] = {0, 0, 0, 0};
     for (int b = t; b < L.nblocks; b += 32)
 #pragma unroll
@@ -454,6 +518,7 @@ clb_status clb_destroy(clb_sim* s) {
     s->dfree(s->buf[0]);
     s->dfree(s->buf[1]);
     s->dfree(s->obs);
+    if (s->hobs) cudaFreeHost(s->hobs);
     s->dfree(s->status);
     s->dfree(s->rc);
     for (cudaGraphExec_t g : s->graph)
@@ -605,11 +670,16 @@ clb_status clb_create(int nx, int ny, double kn, double a, double r, clb_drive d
 
     s->buf[0] = s->dalloc(s->buf_bytes);
     s->buf[1] = s->dalloc(s->buf_bytes);
-    s->obs = static_cast<double*>(s->dalloc(s->L.total * sizeof(double)));
+    s->obs = static_cast<double*>(s->dalloc((s->L.total + 2) * sizeof(double)));
+    if (cudaHostAlloc(reinterpret_cast<void**>(&s->hobs), (s->L.total + 1) * sizeof(double), cudaHostAllocDefault) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        s->hobs = nullptr;
+    }
     s->status = static_cast<unsigned*>(s->dalloc(sizeof(unsigned)));
     s->rc_stride = ((nx + 16 + 31) / 32) * 32;
     s->rc = s->dalloc((size_t)4 * s->rc_stride * (o.storage == CLB_FP64 ? 8 : 4));
-    if (!s->buf[0] || !s->buf[1] || !s->obs || !s->status || !s->rc) {
+    if (!s->buf[0] || !s->buf[1] || !s->obs || !s->hobs || !s->status || !s->rc) {
         clb_destroy(s);
         return fail(CLB_ENOMEM, "clb_create: device allocation of %zu bytes failed", 2 * s->buf_bytes);
     }
@@ -619,7 +689,7 @@ clb_status clb_create(int nx, int ny, double kn, double a, double r, clb_drive d
     };
     chk(cudaMemsetAsync(s->buf[0], 0, s->buf_bytes, s->stream), "memset");
     chk(cudaMemsetAsync(s->buf[1], 0, s->buf_bytes, s->stream), "memset");
-    chk(cudaMemsetAsync(s->obs, 0, s->L.total * sizeof(double), s->stream), "memset");
+    chk(cudaMemsetAsync(s->obs, 0, (s->L.total + 2) * sizeof(double), s->stream), "memset");
     chk(cudaMemsetAsync(s->status, 0, sizeof(unsigned), s->stream), "memset");
     const double rho_slope = (drive == CLB_DRIVE_PRESSURE) ? (s->rho_out - s->rho_in) / (double)(nx - 1) : 0.0;
     chk(cudaMemsetAsync(s->rc, 0, (size_t)4 * s->rc_stride * (o.storage == CLB_FP64 ? 8 : 4), s->stream), "memset");
@@ -791,32 +861,54 @@ clb_status clb_observables(clb_sim* s, int profile_col, clb_scalars* sc, double*
     const double gx = s->drive == CLB_DRIVE_BODY_FORCE ? s->g : 0.0;
     dim3 block(kObsCols, kObsRows);
     dim3 grid(s->L.nblocks);
+    // one launch: the last block sums the partials and takes the status word;
+    // its counter (after the status slot) is cleared first, in case an
+    // earlier launch did not finish
+    unsigned* done = reinterpret_cast<unsigned*>(s->obs + s->L.total + 1);
+    CUDA_OR(cudaMemsetAsync(done, 0, sizeof(unsigned), s->stream));
     CUDA_OR(with_storage(s->storage, [&](auto tag) {
         using T = decltype(tag);
-        obs_kernel<T><<<grid, block, 0, s->stream>>>(static_cast<const T*>(s->buf[s->cur]), s->obs, s->L, nx, ny,
-                                                    s->pitch, s->xoff, s->plane, s->ref0, s->ref_slope, gx, 0.0,
-                                                    profile_col, 1.0 / s->store_scale);
+        auto args = [&](auto kern) {
+            kern<<<grid, block, 0, s->stream>>>(static_cast<const T*>(s->buf[s->cur]), s->obs, s->L, nx, ny, s->pitch,
+                                                s->xoff, s->plane, s->ref0, s->ref_slope, gx, 0.0, profile_col,
+                                                1.0 / s->store_scale, done, s->status, s->obs + s->L.total);
+        };
+        if (s->drive == CLB_DRIVE_BODY_FORCE)
+            args(obs_kernel<T, true>);
+        else
+            args(obs_kernel<T, false>);
         return cudaGetLastError();
     }));
-    obs_final_kernel<<<1, 32, 0, s->stream>>>(s->obs, s->L);
-    CUDA_OR(cudaGetLastError());
-    std::vector<double> h(s->L.part + 4);
-    CUDA_OR(cudaMemcpyAsync(h.data(), s->obs, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    // one pinned copy of what is asked for, one synchronisation: the column
+    // arrays (m(x), centre density) only if an output needs them; the
+    // profiles, the partial sums and the status word always
+    double* h = s->hobs;
+    const bool cols = p_centre || dp_nonlin || m_of_x;
+    if (cols)
+        CUDA_OR(cudaMemcpyAsync(h, s->obs, (size_t)2 * nx * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    CUDA_OR(cudaMemcpyAsync(h + s->L.prof_x, s->obs + s->L.prof_x, ((size_t)2 * ny + 4) * sizeof(double),
+                            cudaMemcpyDeviceToHost, s->stream));
+    CUDA_OR(cudaMemcpyAsync(h + s->L.total, s->obs + s->L.total, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     CUDA_OR(cudaStreamSynchronize(s->stream));
 
-    const double* hm = h.data() + s->L.m;
-    const double* hrc = h.data() + s->L.rc;
-    const double* hux = h.data() + s->L.prof_x;
-    const double* huy = h.data() + s->L.prof_y;
+    const double* hm = h + s->L.m;
+    const double* hrc = h + s->L.rc;
+    const double* hux = h + s->L.prof_x;
+    const double* huy = h + s->L.prof_y;
     const double msum = h[s->L.part + 0], usum = h[s->L.part + 1], mass = h[s->L.part + 2];
     const double nbad = h[s->L.part + 3];
+    const unsigned wait_bits = (unsigned)h[s->L.total];
     const double p_in = s->rho_in / 3.0, p_out = s->rho_out / 3.0;
     const double L = nx > 1 ? (double)(nx - 1) : 1.0;
-    for (int x = 0; x < nx; ++x) {
-        const double pc = hrc[x] / 3.0;
-        if (p_centre) p_centre[x] = pc;
-        if (dp_nonlin) dp_nonlin[x] = (pc - (p_in - (p_in - p_out) * x / L)) / p_out;
-        if (m_of_x) m_of_x[x] = hm[x];
+    if (cols) {
+        // no division per column (the host's divide is slow next to the kernel)
+        const double third = 1.0 / 3.0, slope = (p_in - p_out) / L, ipo = 1.0 / p_out;
+        for (int x = 0; x < nx; ++x) {
+            const double pc = hrc[x] * third;
+            if (p_centre) p_centre[x] = pc;
+            if (dp_nonlin) dp_nonlin[x] = (pc - (p_in - slope * x)) * ipo;
+        }
+        if (m_of_x) std::memcpy(m_of_x, hm, (size_t)nx * sizeof(double));
     }
     double umax = -INFINITY;
     for (int y = 0; y < ny; ++y) {
@@ -847,8 +939,9 @@ clb_status clb_observables(clb_sim* s, int profile_col, clb_scalars* sc, double*
         s->prev_mass_flow = mbar;
         s->have_prev = true;
     }
-    clb_status st = check_status(s, "clb_observables");
-    if (st != CLB_OK) return st;
+    if (wait_bits)
+        return fail(CLB_ETIMEOUT, "clb_observables: a sweep gave up waiting for its staged inputs (bits %u)",
+                    wait_bits);
     if (nbad > 0) return fail(CLB_ENUMERIC, "clb_observables: %.0f nodes with a non-finite density or velocity", nbad);
     return CLB_OK;
 }
@@ -917,7 +1010,7 @@ extern "C" clb_status clb_observables_noalloc(const double* f_dev, int nx, int n
     // the previous call's values stay in the array; start from zeros
     CUDA_OR(cudaMemsetAsync(scratch, 0, L.total * sizeof(double), s));
     // populations in the canonical layout: row pitch nx, no halo, plain FP64 (R = 0)
-    obs_kernel<double><<<dim3(L.nblocks), dim3(kObsCols, kObsRows), 0, s>>>(
+    obs_kernel<double, true><<<dim3(L.nblocks), dim3(kObsCols, kObsRows), 0, s>>>(
         f_dev, scratch, L, nx, ny, nx, 0, (long long)nx * ny, 0.0, 0.0, gx, 0.0, profile_col, 1.0);
     CUDA_OR(cudaGetLastError());
     obs_final_kernel<<<1, 32, 0, s>>>(scratch, L);

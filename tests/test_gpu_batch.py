@@ -5,7 +5,8 @@ from a CUDA graph) against the FP64 oracle, channel by channel.
   nx = 1..7), over a step count that uses both the graph replays and a
   remainder launch: FP64 within 1e-12 per population, FP32-shifted within
   the derived bound of the single-channel tests;
-* every block size gives the same bits (the tile schedule changes who
+* every block size and every schedule (nodes per thread 1, 2, 4, 8, one
+  channel per block or packed) gives the same bits (the schedule changes who
   computes a node, not how); the autotuner leaves the state untouched;
 * the 48-channel sweep of Sec. 3.1 (Kn log-spaced over 0.01..10, ny cycling
   16/32/64/128, G = 1e-6) reaches the oracle's steady normalised flow rate Q
@@ -87,12 +88,45 @@ def test_batch_block_sizes_agree_bitwise(clb):
         b.close()
 
 
+@pytest.mark.parametrize("storage", ["fp32s", "fp64"])
+def test_batch_schedules_agree_bitwise(clb, storage):
+    """Channels of 64 down to 1 node, so that packing puts several in a block."""
+    chans = CHANNELS + [(2, 3, 0.4), (1, 1, 0.7), (4, 8, 0.15), (3, 11, 5.0)]
+    nx = [c[0] for c in chans]
+    ny = [c[1] for c in chans]
+    kn = [c[2] for c in chans]
+    ref = None
+    seen = set()
+    for npt in (1, 2, 4, 8):
+        for packed in (0, 1):
+            b = clb.Batch(nx, ny, kn, g=1e-5, storage=storage, block_x=0)
+            b.set_schedule(npt, packed)
+            sc = b.schedule()
+            assert sc["nodes_per_thread"] == npt and sc["packed"] == packed
+            if packed:
+                assert sc["blocks"] < len(chans)
+            else:
+                assert sc["blocks"] == len(chans)
+            seen.add(sc["blocks"])
+            b.step(777)
+            states = [b.state(k) for k in range(len(chans))]
+            if ref is None:
+                ref = states
+            else:
+                for a, c in zip(ref, states):
+                    np.testing.assert_array_equal(a, c)
+            b.close()
+    assert len(seen) > 2
+
+
 def test_batch_tune_leaves_state(clb):
     b = clb.Batch([4, 4], [16, 128], [0.1, 1.0], g=1e-6, storage="fp32s", block_x=0)
     b.step(10)  # tunes on first use
     before = [b.state(k) for k in range(2)]
     blk = b.tune()
-    assert blk in (64, 128, 256, 512)
+    assert blk % 32 == 0 and 32 <= blk <= 512
+    sc = b.schedule()
+    assert sc["threads_per_block"] == blk and sc["nodes_per_thread"] in (1, 2, 4, 8)
     after = [b.state(k) for k in range(2)]
     for a, c in zip(before, after):
         np.testing.assert_array_equal(a, c)
