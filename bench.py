@@ -74,13 +74,13 @@ def profiled_traffic(storage: str, pipeline: int):
     return profiled_value(storage, pipeline, "traffic_bytes_per_launch")
 
 
-def flops_block(clb, results):
+def flops_block(clb, results, nodes):
     """Measured arithmetic rate of each timed sweep: floating-point operations
     per node update from the SASS counters in the committed ncu summary (None
     where no summary of that kernel on the current sources exists) times the
-    measured node rate, against the fused multiply-add rate clb_peak_fma
-    measures in the sweep's compute precision (FP64 for FP64 storage, FP32
-    otherwise)."""
+    sweeps' own node rate (nodes / sweep_us, the timed region of hbm_frac),
+    against the fused multiply-add rate clb_peak_fma measures in the sweep's
+    compute precision (FP64 for FP64 storage, FP32 otherwise)."""
     peaks = {"f32": clb.clb_peak_fma(clb.CLB_FP32_SHIFTED), "f64": clb.clb_peak_fma(clb.CLB_FP64)}
     out = {"peak_tflops": {k: round(v, 3) for k, v in peaks.items()}, "peak_kind": "measured (clb_peak_fma)"}
     for storage, r in results.items():
@@ -88,7 +88,7 @@ def flops_block(clb, results):
         prec = "f64" if storage == "fp64" else "f32"
         entry = {"precision": prec, "fp_ops_per_node": ops}
         if ops is not None:
-            tf = ops * r["mlups"] * 1e6 / 1e12
+            tf = ops * nodes / (r["sweep_us"] * 1e-6) / 1e12
             entry.update(achieved_tflops=round(tf, 3), frac=round(tf / peaks[prec], 4))
         out[storage] = entry
     return out
@@ -240,12 +240,14 @@ def run_gpu(args):
                 barrier()
         t_total = e0.elapsed_time(e2) / 1e3
         t_sweeps = e0.elapsed_time(e1) / 1e3
+        t_obs = e1.elapsed_time(e2) / 1e3
         t_total = max_over_ranks(t_total, world, "cuda")
         results[storage] = dict(
             pipeline=info["pipeline"],
             mlups=replica_mlups(nodes, K, t_total, world),
             ms_per_step=t_total / K * 1e3,
             sweep_us=t_sweeps / K * 1e6,
+            observables_us=t_obs * 1e6,
             bytes_per_node=info["bytes_per_node"],
             mass_flow=obs["mass_flow"],
             clocks=sampler.summary(),
@@ -320,7 +322,7 @@ def run_gpu(args):
             "kernel": engine_of(f32["pipeline"])["kernel"],
         },
         "variants": variants_block(results, nodes, peak),
-        "flops": flops_block(clb, results),
+        "flops": flops_block(clb, results, nodes),
         "e2e": {
             "value": round(replica_mlups(nodes, K, t_e2e, world), 1),
             "unit": "MLUPS",
@@ -335,13 +337,43 @@ def run_gpu(args):
     if not args.no_batch:
         line["knudsen_sweep"] = knudsen_sweep_bench(clb, torch, args.batch_steps)
         line["small_channel"] = small_channel_bench(clb, torch, args.batch_steps)
+        line["adjoint"] = adjoint_bench(clb, torch)
     if args.no_cpu_baseline or world > 1:
         line["cpu_baseline"] = None
     else:
-        base, ref = cpu_baseline(args.cpu_steps)
+        base, ref = cpu_baseline(args.cpu_steps, args.error_steps)
         line["cpu_baseline"] = base
-        line["errors_vs_oracle"] = errors_vs_oracle(clb, args.variants, ref, args.cpu_steps)
+        line["errors_vs_oracle"] = errors_vs_oracle(clb, args.variants, ref, args.error_steps)
     return line
+
+
+def adjoint_bench(clb, torch):
+    """The adjoint calibration workload of Sec. 3.1: periodic channel nx = 4,
+    ny = 64, Kn = 0.1, G = 1e-6, 20,000 FP32 steps with a checkpoint every 141
+    steps.  Wall time of the checkpointed forward pass and of one backward
+    pass (which recomputes every segment), per step, and the device memory of
+    the states they keep: ceil(N/C) checkpoints + C + 1 segment states + 4
+    adjoint fields, each 9 nx ny FP32 values."""
+    import math
+
+    nx, ny, kn, g, n, every = 4, 64, 0.1, 1e-6, 20000, 141
+    fg = clb.FlowGradient(nx, ny, kn, 2.0, -1.0, g, 1000, storage="fp32s", checkpoint_every=32)  # warm-up
+    fg.q_grad()
+    fg.close()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    fg = clb.FlowGradient(nx, ny, kn, 2.0, -1.0, g, n, storage="fp32s", checkpoint_every=every)
+    t1 = time.perf_counter()
+    grad = fg.q_grad()
+    t2 = time.perf_counter()
+    q = fg.q_norm
+    fg.close()
+    states = math.ceil(n / every) + every + 1 + 4
+    return {"workload": "periodic 4 x 64, Kn 0.1, G 1e-6, 20000 fp32 steps, checkpoint every 141",
+            "forward_ms": round((t1 - t0) * 1e3, 2), "forward_us_per_step": round((t1 - t0) / n * 1e6, 3),
+            "backward_ms": round((t2 - t1) * 1e3, 2), "backward_us_per_step": round((t2 - t1) / n * 1e6, 3),
+            "state_bytes": states * 9 * nx * ny * 4, "states_kept": states, "q_norm": q,
+            "dq_d_r_a_g": grad}
 
 
 def knudsen_sweep_bench(clb, torch, steps):
@@ -365,6 +397,7 @@ def knudsen_sweep_bench(clb, torch, steps):
     t_batch = e0.elapsed_time(e1) / 1e3
     q = [o["q_norm"] for o in b.observables()]
     block = b.info()["block_x"]
+    schedule = b.schedule()
     b.close()
     stream = torch.cuda.Stream()
     chans = [clb.Channel(nx[k], ny[k], kn[k], drive="body_force", drive_value=1e-6, storage="fp32s",
@@ -392,6 +425,7 @@ def knudsen_sweep_bench(clb, torch, steps):
         "us_per_step_separate_launches": round(t_sep / rounds * 1e6, 3),
         "speedup": round((nodes * steps / t_batch) / (nodes * rounds / t_sep), 2),
         "block_x_tuned": block,
+        "schedule_tuned": schedule,
         "steps": steps,
         "q_min_kn_after_steps": kn[i],
     }
@@ -427,7 +461,7 @@ def small_channel_bench(clb, torch, steps):
 
 def errors_vs_oracle(clb, variants, ref, steps):
     """Each storage variant after `steps` steps from the initial state, against
-    the FP64 oracle run of the CPU-baseline leg (same steps, same channel)."""
+    the FP64 oracle run of the CPU-baseline leg continued to the same step."""
     import numpy as np
 
     out = {"steps": steps}
@@ -464,9 +498,14 @@ def engine_of(pipeline: int) -> dict:
 
 
 def variants_block(results, nodes, peak):
+    """Per storage: `mlups` over the whole timed region (K sweeps and one
+    observable reduction read back to the host), `mlups_sweeps` over the
+    sweeps alone (the timed region of `sweep_us` and `hbm_frac`), and the
+    observable reduction's own time."""
     out = {}
     for storage, r in results.items():
-        out[storage] = {"mlups": round(r["mlups"], 1), "sweep_us": round(r["sweep_us"], 3),
+        out[storage] = {"mlups": round(r["mlups"], 1), "mlups_sweeps": round(nodes / r["sweep_us"], 1),
+                        "sweep_us": round(r["sweep_us"], 3), "observables_us": round(r["observables_us"], 1),
                         "pipeline": r["pipeline"],
                         "bytes_per_node": r["bytes_per_node"],
                         "hbm_frac": round(r["bytes_per_node"] * nodes / (r["sweep_us"] * 1e-6) / 1e9 / peak, 4),
@@ -487,10 +526,13 @@ def oracle_sample_run(nx_sample: int, steps: int, threads: int = 0):
     return dt, oracle.threads_used()
 
 
-def cpu_baseline(steps: int = 100):
+def cpu_baseline(steps: int, error_steps: int):
     """The FP64 oracle as it stands, on all host cores, on a bounded sample:
-    `steps` time steps of the full benchmark channel.  Also returns the
-    oracle's state and observables for the error report."""
+    `steps` time steps of the full benchmark channel (timed), continued
+    untimed to `error_steps` for the error report, whose oracle state and
+    observables are returned too.  Sub-entries time the same oracle on one
+    core (a few steps of the same channel) and on the 1601 x 16 channel of
+    Sec. 3.2 (all cores and one core)."""
     import oracle
 
     p = oracle.OracleParams(nx=NX, ny=NY, pressure=True, kn=KN_OUT, rho_in=RATIO, rho_out=1.0)
@@ -499,12 +541,27 @@ def cpu_baseline(steps: int = 100):
     s.step(steps, 0)
     dt = time.perf_counter() - t0
     cores = oracle.threads_used()
+    if error_steps > steps:
+        s.step(error_steps - steps, 0)
     obs = s.observables()
     ref = {"state": s.state(), "mass_flow": obs["mass_flow"], "dp_nonlin": obs["dp_nonlin"]}
     s.close()
     base = {"value": round(NX * NY * steps / dt / 1e6, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
             "sample": f"{steps} time steps of the full {NX}x{NY} channel from the initial state "
                       f"({dt:.1f} s, FP64, OpenMP over rows)"}
+    subs = {}
+    for name, nx, ny, n, threads in (("25601x256_one_core", NX, NY, 4, 1), ("1601x16_all_cores", 1601, 16, 2000, 0),
+                                     ("1601x16_one_core", 1601, 16, 1000, 1)):
+        q = oracle.OracleParams(nx=nx, ny=ny, pressure=True, kn=KN_OUT, rho_in=RATIO if ny == NY else 2.0,
+                                rho_out=1.0)
+        o = oracle.OracleSim(q)
+        t0 = time.perf_counter()
+        o.step(n, threads)
+        t = time.perf_counter() - t0
+        subs[name] = {"value": round(nx * ny * n / t / 1e6, 3), "unit": "MLUPS", "cores": oracle.threads_used(),
+                      "sample": f"{n} steps of the {nx}x{ny} pressure channel ({t:.1f} s)"}
+        o.close()
+    base["more"] = subs
     return base, ref
 
 
@@ -557,8 +614,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10000)
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--cpu-steps", type=int, default=100,
-                    help="oracle steps of the CPU baseline (also the step count of the error report)")
+    ap.add_argument("--cpu-steps", type=int, default=200, help="timed oracle steps of the CPU baseline")
+    ap.add_argument("--error-steps", type=int, default=1000,
+                    help="steps after which every storage is compared with the oracle (>= --cpu-steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variants", default="fp32s,fp64,fp16s,bf16s", help="storages to time (fp32s first)")
     ap.add_argument("--no-batch", action="store_true",
@@ -569,6 +627,7 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    args.error_steps = max(args.error_steps, args.cpu_steps)
     args.variants = [v for v in args.variants.split(",") if v]
     if not args.variants or args.variants[0] != "fp32s":
         ap.error("--variants must start with fp32s (the headline)")
