@@ -53,6 +53,7 @@ struct ObsLayout {
 
 constexpr int kObsCols = 32;  // columns per observable block
 constexpr int kObsRows = 8;   // row groups per observable block
+constexpr int kObsBatch = 4;  // rows a thread loads before reducing them
 
 ObsLayout obs_layout(int nx, int ny) {
     ObsLayout L;
@@ -149,35 +150,39 @@ __global__ void init_kernel(T* f, int nx, int ny, int pitch, int xoff, long long
     }
 }
 
+// The canonical FP64 array [9][ny][nx] <-> the stored state, one row (i, y)
+// per step of blockIdx.y, columns across threads: the row's direction and
+// reference are worked out once per row, and both sides are read and written
+// along x, so `out` / `in` may also be host memory the device can reach
+// (pinned, mapped).
 template <class T>
 __global__ void to_canonical_kernel(const T* f, double* out, int nx, int ny, int pitch, int xoff, long long plane,
                                     double ref0, double ref_slope, double isc) {
-    const long long n = 9LL * ny * nx;
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(idx % nx);
-        const int y = (int)((idx / nx) % ny);
-        const int i = (int)(idx / ((long long)nx * ny));
-        const T* row = f + i * plane + (long long)y * pitch + xoff;
-        out[idx] = c_w[i] * (ref0 + ref_slope * x) + (double)Codec<T>::dec(row[x], RT<T>(isc));
+    for (int row = blockIdx.y; row < 9 * ny; row += gridDim.y) {
+        const int i = row / ny, y = row - i * ny;
+        const T* src = f + i * plane + (long long)y * pitch + xoff;
+        double* dst = out + (long long)row * nx;
+        const double wr0 = c_w[i] * ref0, wrs = c_w[i] * ref_slope;
+        for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < nx; x += gridDim.x * blockDim.x)
+            dst[x] = fma(wrs, (double)x, wr0) + (double)Codec<T>::dec(src[x], RT<T>(isc));
     }
 }
 
 template <class T>
 __global__ void from_canonical_kernel(const double* in, T* f, int nx, int ny, int pitch, int xoff, long long plane,
                                       double ref0, double ref_slope, int periodic, double sc) {
-    const long long n = 9LL * ny * nx;
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(idx % nx);
-        const int y = (int)((idx / nx) % ny);
-        const int i = (int)(idx / ((long long)nx * ny));
-        const T v = Codec<T>::enc(RT<T>(in[idx] - c_w[i] * (ref0 + ref_slope * x)), RT<T>(sc));
-        T* row = f + i * plane + (long long)y * pitch + xoff;
-        row[x] = v;
-        if (periodic) {
-            if (x == 0 && c_ex[i] < 0) row[nx] = v;
-            if (x == nx - 1 && c_ex[i] > 0) row[-1] = v;
+    for (int row = blockIdx.y; row < 9 * ny; row += gridDim.y) {
+        const int i = row / ny, y = row - i * ny;
+        const double* src = in + (long long)row * nx;
+        T* dst = f + i * plane + (long long)y * pitch + xoff;
+        const double wr0 = c_w[i] * ref0, wrs = c_w[i] * ref_slope;
+        for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < nx; x += gridDim.x * blockDim.x) {
+            const T v = Codec<T>::enc(RT<T>(src[x] - fma(wrs, (double)x, wr0)), RT<T>(sc));
+            dst[x] = v;
+            if (periodic) {
+                if (x == 0 && c_ex[i] < 0) dst[nx] = v;
+                if (x == nx - 1 && c_ex[i] > 0) dst[-1] = v;
+            }
         }
     }
 }
@@ -275,43 +280,86 @@ __global__ void __launch_bounds__(kObsCols* kObsRows)
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int x = blockIdx.x * kObsCols + tx;
     double m = 0, us = 0, mass = 0, rc = 0, bad = 0;
+    // centre rows: the middle row, or the two middle rows (averaged)
+    const int yc0 = (ny & 1) ? (ny - 1) / 2 : ny / 2 - 1, yc1 = (ny & 1) ? yc0 : ny / 2;
     if (x < nx) {
         const double ref = ref0 + ref_slope * x;
         const R hgx = R(0.5 * gx), hgy = R(0.5 * gy);
-        const bool want_u = kSumU || x == prof_col;
         RowSum<R> sm, su, sd;
         int rows = 0, nbad = 0;
-#pragma unroll 4
-        for (int y = ty; y < ny; y += kObsRows) {
-            const T* row = f + (long long)y * pitch + xoff + x;
-            R v[9];
+        // density deviations at the centre rows this thread meets (FP32 selects
+        // in the loop; the FP64 arithmetic on them once, after it)
+        R dc0 = 0, dc1 = 0;
+        bool hc0 = false, hc1 = false;
+        // kObsBatch rows' nine values are loaded before any is used, so that
+        // each thread keeps 9 kObsBatch loads in flight; the rows are then
+        // reduced in the same order as one at a time
+        for (int y0 = ty; y0 < ny; y0 += kObsBatch * kObsRows) {
+            T raw[kObsBatch][9];
 #pragma unroll
-            for (int i = 0; i < 9; ++i) v[i] = Codec<T>::dec(row[i * plane], R(isc));
-            const R a57 = v[5] - v[7], a86 = v[8] - v[6];
-            const R drho = v[0] + (v[1] + v[3]) + (v[2] + v[4]) + ((v[5] + v[7]) + (v[6] + v[8]));
-            const R rho = R(ref) + drho;
-            const R mx = (v[1] - v[3]) + (a57 + a86) - hgx * rho;  // rho u_x
-            const R my = (v[2] - v[4]) + (a57 - a86) - hgy * rho;  // rho u_y
-            if (want_u) {
-                const R irho = rcp(rho);
-                const R ux = mx * irho, uy = my * irho;
-                if (!isfinite(rho) || !isfinite(ux) || !isfinite(uy)) ++nbad;
-                su.add(ux);
-                if (x == prof_col) {
-                    obs[L.prof_x + y] = (double)ux;
-                    obs[L.prof_y + y] = (double)uy;
+            for (int b = 0; b < kObsBatch; ++b) {
+                const int y = y0 + b * kObsRows;
+                if (y < ny) {
+                    const T* row = f + (long long)y * pitch + xoff + x;
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) raw[b][i] = row[i * plane];
                 }
-            } else if (!isfinite(rho) || !isfinite(mx) || !isfinite(my) || rho == R(0)) {
-                ++nbad;
             }
-            sm.add(mx);
-            sd.add(drho);
-            ++rows;
-            // centreline: the middle row, or the mean of the two middle rows
-            if (ny & 1) {
-                if (y == (ny - 1) / 2) rc += ref + (double)drho;
-            } else if (y == ny / 2 - 1 || y == ny / 2) {
-                rc += 0.5 * (ref + (double)drho);
+#pragma unroll
+            for (int b = 0; b < kObsBatch; ++b) {
+                const int y = y0 + b * kObsRows;
+                if (y >= ny) break;
+                R v[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) v[i] = Codec<T>::dec(raw[b][i], R(isc));
+                const R a57 = v[5] - v[7], a86 = v[8] - v[6];
+                const R drho = v[0] + (v[1] + v[3]) + (v[2] + v[4]) + ((v[5] + v[7]) + (v[6] + v[8]));
+                const R rho = R(ref) + drho;
+                const R mx = (v[1] - v[3]) + (a57 + a86) - hgx * rho;  // rho u_x
+                const R my = (v[2] - v[4]) + (a57 - a86) - hgy * rho;  // rho u_y
+                if (kSumU) {
+                    const R irho = rcp(rho);
+                    const R ux = mx * irho, uy = my * irho;
+                    if (!isfinite(rho) || !isfinite(ux) || !isfinite(uy)) ++nbad;
+                    su.add(ux);
+                } else if (!isfinite(rho) || !isfinite(mx) || !isfinite(my) || rho == R(0)) {
+                    ++nbad;
+                }
+                sm.add(mx);
+                sd.add(drho);
+                ++rows;
+                if (y == yc0) {
+                    dc0 = drho;
+                    hc0 = true;
+                }
+                if (y == yc1 && yc1 != yc0) {
+                    dc1 = drho;
+                    hc1 = true;
+                }
+            }
+        }
+        // centreline density: the middle row, or the mean of the two middle rows
+        if (ny & 1) {
+            if (hc0) rc += ref + (double)dc0;
+        } else {
+            if (hc0) rc += 0.5 * (ref + (double)dc0);
+            if (hc1) rc += 0.5 * (ref + (double)dc1);
+        }
+        // the velocity profiles at one column: its threads take their rows again
+        if (x == prof_col) {
+            for (int y = ty; y < ny; y += kObsRows) {
+                const T* row = f + (long long)y * pitch + xoff + x;
+                R v[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) v[i] = Codec<T>::dec(row[i * plane], R(isc));
+                const R a57 = v[5] - v[7], a86 = v[8] - v[6];
+                const R drho = v[0] + (v[1] + v[3]) + (v[2] + v[4]) + ((v[5] + v[7]) + (v[6] + v[8]));
+                const R rho = R(ref) + drho;
+                const R mx = (v[1] - v[3]) + (a57 + a86) - hgx * rho;
+                const R my = (v[2] - v[4]) + (a57 - a86) - hgy * rho;
+                const R irho = rcp(rho);
+                obs[L.prof_x + y] = (double)(mx * irho);
+                obs[L.prof_y + y] = (double)(my * irho);
             }
         }
         m = sm.value();
@@ -805,24 +853,44 @@ clb_status clb_info(const clb_sim* s, clb_info_t* info) {
     return CLB_OK;
 }
 
+// Grid of the row-wise conversion kernels.
+static dim3 canon_grid(int nx, int ny) {
+    return dim3((unsigned)std::min(8, (nx + 255) / 256), (unsigned)std::min(9 * ny, 65535));
+}
+
+// The device's address of a host array, if the device can reach it (pinned
+// or registered, and mapped); nullptr for other memory.
+static void* device_view(const void* host) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, host) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 clb_status clb_get_state(clb_sim* s, double* host_f) {
     clb::TraceRange trace_("clb_get_state");
     if (!s || !host_f) return fail(CLB_EINVAL, "clb_get_state: NULL argument");
     const long long n = 9LL * s->nx * s->ny;
-    double* tmp = static_cast<double*>(s->dalloc(n * sizeof(double)));
+    // pinned host memory is written directly by the kernel; other memory
+    // through a transient device buffer
+    double* direct = static_cast<double*>(device_view(host_f));
+    double* tmp = direct ? direct : static_cast<double*>(s->dalloc(n * sizeof(double)));
     if (!tmp) return fail(CLB_ENOMEM, "clb_get_state: device allocation failed");
     clb_status st = CLB_OK;
     cudaError_t e = with_storage(s->storage, [&](auto tag) {
         using T = decltype(tag);
-        to_canonical_kernel<T><<<grid_for(n, 256), 256, 0, s->stream>>>(
+        to_canonical_kernel<T><<<canon_grid(s->nx, s->ny), 256, 0, s->stream>>>(
             static_cast<const T*>(s->buf[s->cur]), tmp, s->nx, s->ny, s->pitch, s->xoff, s->plane, s->ref0,
             s->ref_slope, 1.0 / s->store_scale);
         return cudaGetLastError();
     });
-    if (e == cudaSuccess) e = cudaMemcpyAsync(host_f, tmp, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess && !direct)
+        e = cudaMemcpyAsync(host_f, tmp, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) st = fail(CLB_ECUDA, "clb_get_state: %s", cudaGetErrorString(e));
-    s->dfree(tmp);
+    if (!direct) s->dfree(tmp);
     return st;
 }
 
@@ -830,17 +898,19 @@ clb_status clb_set_state(clb_sim* s, const double* host_f) {
     clb::TraceRange trace_("clb_set_state");
     if (!s || !host_f) return fail(CLB_EINVAL, "clb_set_state: NULL argument");
     const long long n = 9LL * s->nx * s->ny;
-    double* tmp = static_cast<double*>(s->dalloc(n * sizeof(double)));
-    if (!tmp) return fail(CLB_ENOMEM, "clb_set_state: device allocation failed");
+    const double* direct = static_cast<const double*>(device_view(host_f));
+    double* tmp = direct ? nullptr : static_cast<double*>(s->dalloc(n * sizeof(double)));
+    if (!direct && !tmp) return fail(CLB_ENOMEM, "clb_set_state: device allocation failed");
     clb_status st = CLB_OK;
-    cudaError_t e = cudaMemcpyAsync(tmp, host_f, n * sizeof(double), cudaMemcpyHostToDevice, s->stream);
+    cudaError_t e = direct ? cudaSuccess
+                           : cudaMemcpyAsync(tmp, host_f, n * sizeof(double), cudaMemcpyHostToDevice, s->stream);
     const int periodic = s->drive == CLB_DRIVE_BODY_FORCE;
     if (e == cudaSuccess) {
         e = with_storage(s->storage, [&](auto tag) {
             using T = decltype(tag);
-            from_canonical_kernel<T><<<grid_for(n, 256), 256, 0, s->stream>>>(
-                tmp, static_cast<T*>(s->buf[s->cur]), s->nx, s->ny, s->pitch, s->xoff, s->plane, s->ref0,
-                s->ref_slope, periodic, s->store_scale);
+            from_canonical_kernel<T><<<canon_grid(s->nx, s->ny), 256, 0, s->stream>>>(
+                direct ? direct : tmp, static_cast<T*>(s->buf[s->cur]), s->nx, s->ny, s->pitch, s->xoff, s->plane,
+                s->ref0, s->ref_slope, periodic, s->store_scale);
             return cudaGetLastError();
         });
     }

@@ -97,6 +97,13 @@ def test_full_size_short_run(clb, oracle_mod):
     ch32 = clb.Channel(nx, ny, C3["kn_out"], drive="pressure", drive_value=C3["ratio"], storage="fp32s")
     ch32.step(n)
     g32 = ch32.observables()
+    # every population of the whole grid, within the FP32 bound of the parity
+    # tests (c 2^-24 sqrt(n) max|d|, c = 4, d the deviation from w_i R(x))
+    s32 = ch32.state()
+    w = oracle_mod.feq(1.0, 0.0, 0.0)[:, None, None]
+    scale = np.abs(so - w * reference_profile(nx)[None, None, :]).max()
+    assert np.abs(s32 - so).max() <= 4 * 2.0**-24 * np.sqrt(n) * scale
+    del s32
     assert g32["mass_flow"] == pytest.approx(o["mass_flow"], rel=1e-5)
     assert np.abs(g32["m_of_x"] - o["m_of_x"]).max() <= 1e-5 * np.abs(o["m_of_x"]).max()
     assert g32["total_mass"] == pytest.approx(o["total_mass"], rel=1e-9)
