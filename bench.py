@@ -331,7 +331,7 @@ def run_gpu(args):
             "note": "per timed region: upload of the FP64 initial state from pinned host memory, K sweeps, "
                     "observables back to host; bytes per step = bytes per region / K",
         },
-        "gpu_launches": K + 2,
+        "gpu_launches": K + 1,  # K sweeps and one observable reduction
         "clocks": clocks,
     }
     if not args.no_batch:
@@ -351,29 +351,35 @@ def adjoint_bench(clb, torch):
     """The adjoint calibration workload of Sec. 3.1: periodic channel nx = 4,
     ny = 64, Kn = 0.1, G = 1e-6, 20,000 FP32 steps with a checkpoint every 141
     steps.  Wall time of the checkpointed forward pass and of one backward
-    pass (which recomputes every segment), per step, and the device memory of
-    the states they keep: ceil(N/C) checkpoints + C + 1 segment states + 4
-    adjoint fields, each 9 nx ny FP32 values."""
+    pass (which recomputes every segment), per step, for the default engine
+    (the grid fits in shared memory: one block per pass) and for one launch
+    per step; and the device memory of the states they keep: ceil(N/C)
+    checkpoints + C + 1 segment states + 4 adjoint fields, each 9 nx ny FP32
+    values."""
     import math
 
     nx, ny, kn, g, n, every = 4, 64, 0.1, 1e-6, 20000, 141
-    fg = clb.FlowGradient(nx, ny, kn, 2.0, -1.0, g, 1000, storage="fp32s", checkpoint_every=32)  # warm-up
-    fg.q_grad()
-    fg.close()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    fg = clb.FlowGradient(nx, ny, kn, 2.0, -1.0, g, n, storage="fp32s", checkpoint_every=every)
-    t1 = time.perf_counter()
-    grad = fg.q_grad()
-    t2 = time.perf_counter()
-    q = fg.q_norm
-    fg.close()
+    out = {"workload": "periodic 4 x 64, Kn 0.1, G 1e-6, 20000 fp32 steps, checkpoint every 141"}
+    for name, pipeline in (("resident", 0), ("launch_per_step", 1)):
+        fg = clb.FlowGradient(nx, ny, kn, 2.0, -1.0, g, 1000, storage="fp32s", checkpoint_every=32,
+                              pipeline=pipeline)  # warm-up
+        fg.q_grad()
+        fg.close()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fg = clb.FlowGradient(nx, ny, kn, 2.0, -1.0, g, n, storage="fp32s", checkpoint_every=every,
+                              pipeline=pipeline)
+        t1 = time.perf_counter()
+        grad = fg.q_grad()
+        t2 = time.perf_counter()
+        q = fg.q_norm
+        fg.close()
+        out[name] = {"forward_ms": round((t1 - t0) * 1e3, 2), "forward_us_per_step": round((t1 - t0) / n * 1e6, 3),
+                     "backward_ms": round((t2 - t1) * 1e3, 2),
+                     "backward_us_per_step": round((t2 - t1) / n * 1e6, 3), "q_norm": q, "dq_d_r_a_g": grad}
     states = math.ceil(n / every) + every + 1 + 4
-    return {"workload": "periodic 4 x 64, Kn 0.1, G 1e-6, 20000 fp32 steps, checkpoint every 141",
-            "forward_ms": round((t1 - t0) * 1e3, 2), "forward_us_per_step": round((t1 - t0) / n * 1e6, 3),
-            "backward_ms": round((t2 - t1) * 1e3, 2), "backward_us_per_step": round((t2 - t1) / n * 1e6, 3),
-            "state_bytes": states * 9 * nx * ny * 4, "states_kept": states, "q_norm": q,
-            "dq_d_r_a_g": grad}
+    out.update(state_bytes=states * 9 * nx * ny * 4, states_kept=states)
+    return out
 
 
 def knudsen_sweep_bench(clb, torch, steps):

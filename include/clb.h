@@ -314,7 +314,13 @@ typedef struct clb_adjoint clb_adjoint; /* opaque */
  * CLB_FP32_SHIFTED (states and adjoints in that precision; the parameter
  * sums are FP64).  r < 0 takes r_b from Eq. 21 with opts->sigma (the gradient
  * is still with respect to r_b).  Device memory: (ceil(nsteps/C) + C + 5)
- * states of 9 nx ny elements.  Synchronises.  nx * ny <= 2^22. */
+ * states of 9 nx ny elements.  Synchronises.  nx * ny <= 2^22.
+ * Engine: a grid whose two states fit in one block's shared memory
+ * (2 * 9 nx ny elements <= about 200 KB: 2800 nodes in FP32) runs the
+ * forward pass as one launch of one block and each backward pass as one
+ * launch of an 8-block cluster; larger grids, or opts->pipeline = 1, use one
+ * launch per step.  Both give the same states; the FP64 sums of J and of the
+ * gradient are taken in different orders. */
 clb_status clb_adjoint_forward(int nx, int ny, double kn, double a, double r, double g, int64_t nsteps,
                                int checkpoint_every, const clb_opts* opts, clb_adjoint** out, double* J);
 

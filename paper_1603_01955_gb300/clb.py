@@ -520,7 +520,7 @@ class FlowGradient:
     Q of Sec. 3.1 and its gradient come from the library as well."""
 
     def __init__(self, nx, ny, kn, a, r, g, nsteps, storage="fp32s", checkpoint_every=0, b2=0.55, sigma=1.0,
-                 s3=1.1, s8=1.2, rho_out=1.0, stream=None):
+                 s3=1.1, s8=1.2, rho_out=1.0, stream=None, pipeline=0):
         import torch
 
         dev = torch.cuda.current_device()
@@ -531,6 +531,7 @@ class FlowGradient:
         o.b2, o.sigma, o.s3, o.s8, o.rho_out = b2, sigma, s3, s8, rho_out
         o.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
         o.stream = C.c_void_p(stream.cuda_stream)
+        o.pipeline = int(pipeline)  # 1: one launch per step instead of one block per pass
 
         def _alloc(nbytes, ctx):
             try:

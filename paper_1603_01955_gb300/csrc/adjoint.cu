@@ -268,6 +268,230 @@ __global__ void __launch_bounds__(kAdjThreads) adj_final_kernel(const R* f, R* l
     if (threadIdx.x == 0) acc[3 * gridDim.x + blockIdx.x] = js;
 }
 
+// ------------------------------------------------------ resident engine
+//
+// For a grid whose two states fit in one block's shared memory, the whole
+// checkpointed forward pass is one launch of one block, with block barriers
+// between the steps; the backward walk over every segment is one launch of a
+// thread-block cluster, with cluster barriers between its phases (the
+// arithmetic is that of the kernels above).  In the backward step the 9 + 2
+// forward-mode columns of each node's collision are spread over separate
+// threads.  The parameter sums stay per thread (FP64, in step order) and are
+// added by fixed trees at the end, so the gradient is the same bit for bit on
+// every run.
+constexpr int kResThreads = 256;  // the dual-number collision needs ~160-250 registers
+constexpr int kCols = 11;         // 9 population tangents, then a and G
+
+__device__ __forceinline__ double res_block_sum(double v, double* sh) {
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int w = kResThreads / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// One step of the whole grid in shared memory, a -> b (and optionally to a
+// global copy `out`).
+template <class R>
+__device__ __forceinline__ void res_step(const R* a, R* b, R* out, const AdjConst<R>& k) {
+    const int nn = k.nx * k.ny;
+    for (int node = threadIdx.x; node < nn; node += kResThreads) {
+        R d[9];
+        pull(a, k.nx, k.ny, node % k.nx, node / k.nx, k.r, k.rc, d);
+        collide<R, MODE_PERIODIC>(d, k.ref, k.c);
+        for (int i = 0; i < 9; ++i) {
+            b[i * nn + node] = d[i];
+            if (out) out[i * nn + node] = d[i];
+        }
+    }
+}
+
+// Forward pass from f^eq(rho_out, 0): checkpoint s (the state at step s C)
+// into ckpt + s state_elems, then J and lambda_N (as adj_final_kernel).
+template <class R>
+__global__ void __launch_bounds__(kResThreads)
+    adj_res_forward_kernel(R* ckpt, size_t state_elems, int every, long long nsteps, R* lam_final, double* J,
+                           AdjConst<R> k) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    const int nn = k.nx * k.ny, n9 = 9 * nn;
+    R* a = reinterpret_cast<R*>(sm_raw);
+    R* b = a + n9;
+    double* red = reinterpret_cast<double*>(sm_raw + ((2 * n9 * sizeof(R) + 15) / 16) * 16);
+    for (int e = threadIdx.x; e < n9; e += kResThreads) a[e] = R(0);  // zero deviations
+    __syncthreads();
+    for (long long t = 0; t < nsteps; ++t) {
+        if (t % every == 0) {
+            R* c = ckpt + (size_t)(t / every) * state_elems;
+            for (int e = threadIdx.x; e < n9; e += kResThreads) c[e] = a[e];
+        }
+        res_step<R>(a, b, nullptr, k);
+        __syncthreads();
+        R* t2 = a;
+        a = b;
+        b = t2;
+    }
+    const int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    double js = 0;
+    for (int node = threadIdx.x; node < nn; node += kResThreads) {
+        double rho = (double)k.ref, jx = 0;
+        for (int i = 0; i < 9; ++i) {
+            const double v = (double)a[i * nn + node];
+            rho += v;
+            jx += ex[i] * v;
+        }
+        const double ux = jx / rho - 0.5 * (double)k.c.fx;
+        js += ux / k.nx;
+        for (int i = 0; i < 9; ++i) lam_final[i * nn + node] = R((ex[i] - ux - 0.5 * (double)k.c.fx) / (k.nx * rho));
+    }
+    js = res_block_sum(js, red);
+    if (threadIdx.x == 0) *J = js;
+}
+
+// The backward walk over every segment, spread over one thread-block cluster
+// of `gridDim.x` blocks: recompute the segment's states from its checkpoint,
+// then per step mu_t = J_C^T lambda_{t+1}, one thread per node and column,
+// with lambda_{t+1} = P^T mu_{t+1} gathered on the fly from the previous
+// step's mu (lambda_N itself for the first step), so one cluster barrier
+// separates the steps.  mu (two buffers) and the segment states are in global
+// memory (a few KB each, resident in L2); the cluster barrier (release /
+// acquire at cluster scope) orders them.  Every block runs the same loop
+// counts, so every barrier is reached by all of them.  Each block's
+// parameter sums go to part[rank * 3 + 0..2], added on the host in rank order.
+constexpr int kClusterMax = 16;
+
+__device__ __forceinline__ void cluster_barrier() {
+    __threadfence();
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ int cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return (int)r;
+}
+
+// lambda_t(node) = (P^T mu)(node): each post-collision population of step t is
+// pulled by the node it streams to, or, at a wall, by the bounce-back and the
+// specular terms of Eq. 20 (as adj_transpose_kernel).
+template <class R>
+__device__ __forceinline__ void transpose_at(const R* mu, int nx, int ny, int x, int y, R r, R rc, R (&o)[9]) {
+    const int nn = nx * ny;
+    const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+    auto M = [&](int i, int yy, int xx) -> R { return mu[i * nn + yy * nx + xx]; };
+    o[0] = M(0, y, x);
+    o[1] = M(1, y, xp);
+    o[3] = M(3, y, xm);
+    if (y == ny - 1) {
+        o[2] = M(4, y, x);
+        o[5] = r * M(7, y, x) + rc * M(8, y, xp);
+        o[6] = r * M(8, y, x) + rc * M(7, y, xm);
+    } else {
+        o[2] = M(2, y + 1, x);
+        o[5] = M(5, y + 1, xp);
+        o[6] = M(6, y + 1, xm);
+    }
+    if (y == 0) {
+        o[4] = M(2, 0, x);
+        o[7] = r * M(5, 0, x) + rc * M(6, 0, xm);
+        o[8] = r * M(6, 0, x) + rc * M(5, 0, xp);
+    } else {
+        o[4] = M(4, y - 1, x);
+        o[7] = M(7, y - 1, xm);
+        o[8] = M(8, y - 1, xp);
+    }
+}
+
+template <class R>
+__global__ void __launch_bounds__(kResThreads)
+    adj_cl_backward_kernel(const R* ckpt, R* seg, size_t state_elems, int every, long long nsteps,
+                           const R* lam_final, R* mu0, R* mu1, double* part, AdjConst<R> k) {
+    __shared__ double red[kResThreads];
+    const int nn = k.nx * k.ny, n9 = 9 * nn, nx = k.nx, ny = k.ny;
+    const int rank = cluster_rank();
+    const int g0 = rank * kResThreads + (int)threadIdx.x, gs = (int)gridDim.x * kResThreads;
+    double gr = 0, ga = 0, gg = 0;
+    const R* mu_next = nullptr;  // mu of step t + 1 (none before the first backward step)
+    R* mu_cur = mu0;
+    const long long nseg = (nsteps + every - 1) / every;
+    for (long long s = nseg - 1; s >= 0; --s) {
+        const long long t0 = s * every;
+        const int len = (int)min((long long)every, nsteps - t0);
+        const R* c = ckpt + (size_t)s * state_elems;
+        for (int e = g0; e < n9; e += gs) seg[e] = c[e];
+        cluster_barrier();
+        for (int j = 1; j < len; ++j) {  // recompute the segment's states
+            const R* a = seg + (size_t)(j - 1) * state_elems;
+            R* b = seg + (size_t)j * state_elems;
+            for (int node = g0; node < nn; node += gs) {
+                R d[9];
+                pull(a, nx, ny, node % nx, node / nx, k.r, k.rc, d);
+                collide<R, MODE_PERIODIC>(d, k.ref, k.c);
+                for (int i = 0; i < 9; ++i) b[i * nn + node] = d[i];
+            }
+            cluster_barrier();
+        }
+        for (int j = len - 1; j >= 0; --j) {
+            const R* ft = seg + (size_t)j * state_elems;
+            for (int it = g0; it < nn * kCols; it += gs) {
+                const int node = it / kCols, col = it - node * kCols;
+                const int x = node % nx, y = node / nx;
+                R lam[9];
+                if (mu_next) {
+                    transpose_at(mu_next, nx, ny, x, y, k.r, k.rc, lam);
+                } else {
+                    for (int i = 0; i < 9; ++i) lam[i] = lam_final[i * nn + node];
+                }
+                R fb[9];
+                pull(ft, nx, ny, x, y, k.r, k.rc, fb);
+                const KC<Dual<R>> cd = dual_consts(k, col < 9 ? 0 : col - 8);
+                Dual<R> d[9];
+                for (int i = 0; i < 9; ++i) d[i] = Dual<R>(fb[i], i == col ? R(1) : R(0));
+                collide<Dual<R>, MODE_PERIODIC>(d, Dual<R>(k.ref, R(0)), cd);
+                if (col < 9) {
+                    R m = 0;
+                    for (int i = 0; i < 9; ++i) m += lam[i] * d[i].d;
+                    mu_cur[col * nn + node] = m;
+                    // dP/dr at the wall rows (Eq. 20)
+                    const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+                    auto at = [&](int i, int xx) -> double { return (double)ft[i * nn + y * nx + xx]; };
+                    if (y == 0 && col == 5) gr += (double)m * (at(7, x) - at(8, xm));
+                    if (y == 0 && col == 6) gr += (double)m * (at(8, x) - at(7, xp));
+                    if (y == ny - 1 && col == 7) gr += (double)m * (at(5, x) - at(6, xp));
+                    if (y == ny - 1 && col == 8) gr += (double)m * (at(6, x) - at(5, xm));
+                } else {
+                    double sum = 0;
+                    for (int i = 0; i < 9; ++i) sum += (double)lam[i] * (double)d[i].d;
+                    if (col == 9)
+                        ga += sum;
+                    else
+                        gg += sum;
+                }
+            }
+            cluster_barrier();
+            mu_next = mu_cur;
+            mu_cur = mu_cur == mu0 ? mu1 : mu0;
+        }
+    }
+    gr = res_block_sum(gr, red);
+    ga = res_block_sum(ga, red);
+    gg = res_block_sum(gg, red);
+    if (threadIdx.x == 0) {
+        part[rank * 3 + 0] = gr;
+        part[rank * 3 + 1] = ga;
+        part[rank * 3 + 2] = gg;
+    }
+}
+
+// Shared memory of the resident forward kernel: two states and the block sum.
+size_t res_smem(int nx, int ny, size_t elem) {
+    return ((2 * 9 * (size_t)nx * ny * elem + 15) / 16) * 16 + kResThreads * sizeof(double);
+}
+constexpr size_t kResSmemCap = 200 * 1024;
+
 }  // namespace
 
 struct clb_adjoint {
@@ -283,6 +507,8 @@ struct clb_adjoint {
     void* mu = nullptr;
     double* acc = nullptr; // per-block partial sums [4][nb]: r, a, G and J
     int nb = 0;            // blocks of every adjoint launch
+    bool resident = false; // resident engine: the forward pass in one block, the backward in one cluster
+    int cluster = 0;       // blocks of the backward cluster (0: not yet launched)
     AdjConst<float> kf;
     AdjConst<double> kd;
     double J = 0;
@@ -338,7 +564,80 @@ cudaError_t sum_partials(clb_adjoint* h, int rows, double* out) {
     return cudaSuccess;
 }
 
+template <class R> cudaError_t set_res_smem(size_t bytes) {
+    return cudaFuncSetAttribute(adj_res_forward_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// Both passes in one block each (resident engine).
+template <class R> cudaError_t forward_resident(clb_adjoint* h) {
+    const size_t smem = res_smem(h->nx, h->ny, sizeof(R));
+    cudaError_t e = set_res_smem<R>(smem);
+    if (e != cudaSuccess) return e;
+    adj_res_forward_kernel<R><<<1, kResThreads, smem, h->stream>>>(
+        static_cast<R*>(h->ckpt), h->state_elems, h->every, (long long)h->nsteps, static_cast<R*>(h->lam_final),
+        h->acc, kconst<R>(h));
+    e = cudaGetLastError();
+    double J = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&J, h->acc, sizeof J, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess) h->J = J;
+    return e;
+}
+
+// Launch the cluster backward kernel with `cl` blocks (16 needs the
+// non-portable cluster size, which the device may refuse).
+template <class R> cudaError_t launch_cl_backward(clb_adjoint* h, int cl) {
+    auto kern = adj_cl_backward_kernel<R>;
+    if (cl > 8) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cl);
+    cfg.blockDim = dim3(kResThreads);
+    cfg.stream = h->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<const R*>(h->ckpt), static_cast<R*>(h->seg), h->state_elems,
+                              h->every, (long long)h->nsteps, static_cast<const R*>(h->lam_final),
+                              static_cast<R*>(h->lam[0]), static_cast<R*>(h->mu), h->acc, kconst<R>(h));
+}
+
+template <class R> cudaError_t backward_resident(clb_adjoint* h, double* out3) {
+    // the largest cluster the device runs (16 blocks, else the portable 8)
+    int cl = h->cluster;
+    cudaError_t e = cudaSuccess;
+    if (cl == 0) {
+        cl = kClusterMax;
+        e = launch_cl_backward<R>(h, cl);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            cl = 8;
+            e = launch_cl_backward<R>(h, cl);
+        }
+        if (e == cudaSuccess) h->cluster = cl;
+    } else {
+        e = launch_cl_backward<R>(h, cl);
+    }
+    double part[3 * kClusterMax];
+    if (e == cudaSuccess) e = cudaMemcpyAsync(part, h->acc, 3 * cl * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return e;
+    for (int q = 0; q < 3; ++q) {
+        double v = 0;
+        for (int r = 0; r < cl; ++r) v += part[r * 3 + q];  // rank order
+        out3[q] = v;
+    }
+    return cudaSuccess;
+}
+
 template <class R> cudaError_t forward_run(clb_adjoint* h) {
+    if (h->resident) return forward_resident<R>(h);
     const AdjConst<R>& k = kconst<R>(h);
     const int nb = h->nb;
     R* cur = state_at<R>(h->seg, h->state_elems, 0);
@@ -367,6 +666,15 @@ template <class R> cudaError_t forward_run(clb_adjoint* h) {
 }
 
 template <class R> cudaError_t backward_run(clb_adjoint* h, double seed, double grad[3]) {
+    if (h->resident) {
+        double hacc[3];
+        cudaError_t e = backward_resident<R>(h, hacc);
+        if (e != cudaSuccess) return e;
+        grad[0] = seed * hacc[0];
+        grad[1] = seed * hacc[1];
+        grad[2] = seed * (hacc[2] - 0.5 * h->ny);
+        return cudaSuccess;
+    }
     const AdjConst<R>& k = kconst<R>(h);
     const int nb = h->nb;
     cudaError_t e = cudaMemsetAsync(h->acc, 0, (size_t)3 * nb * sizeof(double), h->stream);
@@ -502,7 +810,10 @@ clb_status clb_adjoint_forward(int nx, int ny, double kn, double a, double r, do
     h->lam_final = h->dalloc(sb);
     h->mu = h->dalloc(sb);
     h->nb = blocks_for((size_t)nx * ny, kAdjThreads);
-    h->acc = static_cast<double*>(h->dalloc((size_t)4 * h->nb * sizeof(double)));
+    // one block per pass when the grid fits in its shared memory, unless
+    // opts->pipeline asks for one launch per step (1)
+    h->resident = o.pipeline != 1 && res_smem(nx, ny, h->elem) <= kResSmemCap;
+    h->acc = static_cast<double*>(h->dalloc(std::max<size_t>(4 * (size_t)h->nb, 3 * kClusterMax) * sizeof(double)));
     if (!h->ckpt || !h->seg || !h->lam[0] || !h->lam[1] || !h->lam_final || !h->mu || !h->acc) {
         clb_adjoint_destroy(h);
         return (clb_status)set_error(CLB_ENOMEM, "clb_adjoint_forward: device allocation failed");

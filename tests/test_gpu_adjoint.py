@@ -108,6 +108,24 @@ def test_flow_rate_autograd(clb):
     fg.close()
 
 
+@pytest.mark.parametrize("storage,tol", [("fp64", 1e-12), ("fp32s", 1e-5)])
+@pytest.mark.parametrize("nx,ny,n,every", [(4, 16, 700, 31), (3, 5, 1000, 0), (4, 64, 2000, 45)])
+def test_resident_engine_matches_per_step_launches(clb, storage, tol, nx, ny, n, every):
+    """The one-block-per-pass engine (grids that fit in shared memory) and the
+    one-launch-per-step engine compute the same states; only the order of the
+    FP64 sums of J and of the gradient differs."""
+    out = []
+    for pipeline in (0, 1):
+        fg = clb.FlowGradient(nx, ny, 0.3, 2.0, 0.8, 2e-5, n, storage=storage, checkpoint_every=every,
+                              pipeline=pipeline)
+        out.append((fg.J, fg.grad()))
+        fg.close()
+    (j0, g0), (j1, g1) = out
+    assert j0 == pytest.approx(j1, rel=tol)
+    for a, b in zip(g0, g1):
+        assert a == pytest.approx(b, rel=tol)
+
+
 def test_q_and_its_gradient_match_oracle(clb, oracle_mod):
     """Q (clb_adjoint_q) against the oracle's own Q observable, and dQ/d(r_b,
     a, G) (clb_adjoint_q_backward) against the oracle's complex-step dJ
