@@ -79,6 +79,17 @@ MUTANTS = [
      "const real_t sb = 2.0 * ucol_prof[0] - 1.0 * ucol_prof[1];"),
     ("slip_extrapolated_to_J0_top", "const real_t st = 1.5 * ucol_prof[3] - 0.5 * ucol_prof[2];",
      "const real_t st = 2.0 * ucol_prof[3] - 1.0 * ucol_prof[2];"),
+    # centreline Knudsen number (Sec. 3.2, reading R8): the row, the time level, the mode itself
+    ("centreline_wrong_row", "        const int y1 = (ny % 2) ? y0 : ny / 2;\n        for (int i = 0; i < NQ; ++i) {",
+     "        const int y1 = (ny % 2) ? y0 : ny / 2 + 1;\n        for (int i = 0; i < NQ; ++i) {"),
+    ("centreline_of_the_streamed_state",
+     "        centreline_density(&s->p, s->ft, s->rc); /* of the state before the step */\n"
+     "        stream_and_boundaries(&s->p, s->ft, s->fb, nthreads);",
+     "        stream_and_boundaries(&s->p, s->ft, s->fb, nthreads);\n"
+     "        centreline_density(&s->p, s->fb, s->rc);"),
+    ("centreline_mode_ignored",
+     "node_rates(p, (p->pressure && p->kn_mode == 1) ? rc[x] : raw_moment(f, 0, 0), s);",
+     "node_rates(p, raw_moment(f, 0, 0), s);"),
     # complex-step derivative (the reference of the adjoint)
     ("complex_step_drops_r", "static real_t P_r(const oracle_params* p) { return p->r + I * p->r_im; }",
      "static real_t P_r(const oracle_params* p) { return p->r; }"),
