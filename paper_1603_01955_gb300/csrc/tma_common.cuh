@@ -168,19 +168,6 @@ __device__ __forceinline__ void load_tile(const SweepArgs& a, const Field<T> f, 
     }
 }
 
-// A pressure column node (Sec. 3.2): rebuilt pre-collision populations,
-// collided and stored to `out` (element i at out[i * plane]).
-template <class T, int MODE>
-__device__ __noinline__ void boundary_node(const SweepArgs& a, const KC<typename Codec<T>::R>& c, const Field<T> src,
-                                           int x, int y, bool inlet, T* out, long long plane) {
-    using R = typename Codec<T>::R;
-    R d[9];
-    rebuild_column<T, R>(a, c, src, x, y, inlet, d);
-    collide<R, MODE>(d, ln::fma(c.slope, R(x), c.ref0), c);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) out[i * plane] = Raw<T>::enc(d[i]);
-}
-
 // One consumer thread's share of a staged tile: nodes x0 .. x0+V-1 of row y
 // (x0 = tile start + thread * V).  The row's wall bits and the columns' inlet,
 // outlet and halo roles follow from the indices (x = 0 and x = nx - 1; y = 0
@@ -200,10 +187,6 @@ __device__ __forceinline__ void tile_update(const SweepArgs& a, const KC<typenam
     const int rt = row_kind(y, a.ny);
     constexpr int E = 16 / (int)sizeof(T);
     constexpr bool kShift = (MODE == MODE_PRESSURE) && !std::is_same<T, double>::value;
-    // the 16-bit sweeps, which collide pairs of nodes in packed FP32, add the
-    // shifts of the pulled values (away from the wall terms) as packed adds too
-    constexpr bool kPackPair = Pair16<T>::ok && V % 2 == 0;
-    constexpr bool kLaneShift = kShift && !kPackPair;
     // The thread's window of slot i, columns x0 - 1 .. x0 + V (index k + 1):
     // the V middle values in one aligned vector load, an end value only for the
     // slots that pull from it (e_x = +1 from the left, e_x = -1 from the right;
@@ -246,7 +229,7 @@ __device__ __forceinline__ void tile_update(const SweepArgs& a, const KC<typenam
             f[2][k] = at(2, k);
             f[5][k] = at(5, k - 1);
             f[6][k] = at(6, k + 1);
-            if (kLaneShift) {
+            if (kShift) {
                 f[5][k] += c.shd;
                 f[6][k] -= c.shd;
             }
@@ -259,12 +242,12 @@ __device__ __forceinline__ void tile_update(const SweepArgs& a, const KC<typenam
             f[4][k] = at(4, k);
             f[7][k] = at(7, k + 1);
             f[8][k] = at(8, k - 1);
-            if (kLaneShift) {
+            if (kShift) {
                 f[7][k] -= c.shd;
                 f[8][k] += c.shd;
             }
         }
-        if (kLaneShift) {
+        if (kShift) {
             f[1][k] += c.sha;
             f[3][k] -= c.sha;
         }
@@ -275,31 +258,39 @@ __device__ __forceinline__ void tile_update(const SweepArgs& a, const KC<typenam
     // the thread's node in the first and in the last column, if any (x0 < nx)
     const int kfirst = x0 == 0 ? 0 : -1;
     const int klast = a.nx - 1 - x0 < V ? a.nx - 1 - x0 : -1;
+    if (MODE == MODE_PRESSURE) {
+        const int kin = kfirst, kout = klast;  // inlet x = 0, outlet x = nx - 1
+        if (kin >= 0) {
+            R t[9];
+            rebuild_column<T, R>(a, c, src, x0 + kin, y, true, t);
+#pragma unroll
+            for (int k = 0; k < V; ++k)
+                if (k == kin)
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) f[i][k] = t[i];
+        }
+        if (kout >= 0) {
+            R t[9];
+            rebuild_column<T, R>(a, c, src, x0 + kout, y, false, t);
+#pragma unroll
+            for (int k = 0; k < V; ++k)
+                if (k == kout)
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) f[i][k] = t[i];
+        }
+    }
     // The 16-bit sweeps are bound by instruction issue as much as by HBM, so
     // they collide nodes k and k + 1 together in packed FP32 (bit for bit the
     // scalar collision, with about a third fewer instructions per node).  The
     // FP32 sweep is bound by HBM alone: there the packed form finished its
     // arithmetic sooner but moved the bytes less evenly, and back-to-back
     // steps got slower, so it collides one node per lane.
-    if constexpr (kPackPair) {
+    if constexpr (Pair16<T>::ok && V % 2 == 0) {
 #pragma unroll
         for (int k = 0; k < V; k += 2) {
             float2 d[9];
 #pragma unroll
             for (int i = 0; i < 9; ++i) d[i] = make_float2(f[i][k], f[i][k + 1]);
-            if constexpr (kShift) {  // each lane rounded as the scalar add it replaces
-                const float2 sa = ln::bc<float2>(c.sha), sd = ln::bc<float2>(c.shd);
-                d[1] = ln::add(d[1], sa);
-                d[3] = ln::sub(d[3], sa);
-                if (!(rt & ROW_BOTTOM)) {
-                    d[5] = ln::add(d[5], sd);
-                    d[6] = ln::sub(d[6], sd);
-                }
-                if (!(rt & ROW_TOP)) {
-                    d[7] = ln::sub(d[7], sd);
-                    d[8] = ln::add(d[8], sd);
-                }
-            }
             const float2 ref = (MODE == MODE_PRESSURE)
                                    ? ln::fma(ln::bc<float2>(c.slope), make_float2(float(x0 + k), float(x0 + k + 1)),
                                              ln::bc<float2>(c.ref0))
@@ -364,16 +355,6 @@ __device__ __forceinline__ void tile_update(const SweepArgs& a, const KC<typenam
                 orow[8 * P - 1] = Raw<T>::enc(f[8][k]);
             }
         }
-    } else {
-        // Pressure inlet (x = 0) and outlet (x = nx - 1): the values just
-        // stored there came from pulled populations; rebuild the column's
-        // pre-collision populations (Sec. 3.2), collide that node alone and
-        // overwrite them.  Done after the store, when the thread's other
-        // values are no longer live, so the rare rebuild does not raise the
-        // register count of every thread; a lane collides the same bits alone
-        // as packed, so the results equal a rebuild before the collision.
-        if (kfirst >= 0) boundary_node<T, MODE>(a, c, src, x0 + kfirst, y, true, orow + x0 + kfirst, P);
-        if (klast >= 0) boundary_node<T, MODE>(a, c, src, x0 + klast, y, false, orow + x0 + klast, P);
     }
 }
 
