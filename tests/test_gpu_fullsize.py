@@ -104,6 +104,17 @@ def test_full_size_short_run(clb, oracle_mod):
     scale = np.abs(so - w * reference_profile(nx)[None, None, :]).max()
     assert np.abs(s32 - so).max() <= 4 * 2.0**-24 * np.sqrt(n) * scale
     del s32
+    ch32.close()
+    # the 16-bit storages: the same bound with their unit round-off (FP16 x 2^14: 2^-11,
+    # BF16: 2^-8); their mass flow is reported, not bounded at 1e-5
+    for storage, u in (("fp16s", 2.0**-11), ("bf16s", 2.0**-8)):
+        ch = clb.Channel(nx, ny, C3["kn_out"], drive="pressure", drive_value=C3["ratio"], storage=storage)
+        ch.step(n)
+        s16 = ch.state()
+        ch.close()
+        err = np.abs(s16 - so).max()
+        del s16
+        assert err <= 4 * u * np.sqrt(n) * scale, (storage, err / scale)
     assert g32["mass_flow"] == pytest.approx(o["mass_flow"], rel=1e-5)
     assert np.abs(g32["m_of_x"] - o["m_of_x"]).max() <= 1e-5 * np.abs(o["m_of_x"]).max()
     assert g32["total_mass"] == pytest.approx(o["total_mass"], rel=1e-9)
