@@ -720,6 +720,7 @@ clb_status clb_batch_tune(clb_batch* b, int* block_out) {
             BatchSched sc;
             if (make_sched(b, npt, packed, 0, sc) != CLB_OK) {
                 set_error(CLB_OK, "%s", "");  // an infeasible schedule is not an error of the tuner
+                if (!packed) unpacked_blocks = -1;
                 continue;
             }
             if (!packed) unpacked_blocks = sc.nblocks;
