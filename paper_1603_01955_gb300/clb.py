@@ -333,11 +333,12 @@ class Channel:
 
     def observables(self, profile_col=-1, check=True) -> dict:
         s = clb_scalars()
-        ux = np.zeros(self.ny)
-        uy = np.zeros(self.ny)
-        pc = np.zeros(self.nx)
-        dp = np.zeros(self.nx)
-        mx = np.zeros(self.nx)
+        # the library writes every element of every output (np.empty: no page-zeroing pass)
+        ux = np.empty(self.ny)
+        uy = np.empty(self.ny)
+        pc = np.empty(self.nx)
+        dp = np.empty(self.nx)
+        mx = np.empty(self.nx)
         st = clb_observables(self.sim, profile_col, s, ux, uy, pc, dp, mx, check=check)
         out = {k: getattr(s, k) for k, _ in clb_scalars._fields_}
         out.update(ux_prof=ux, uy_prof=uy, p_centre=pc, dp_nonlin=dp, m_of_x=mx, status=st)

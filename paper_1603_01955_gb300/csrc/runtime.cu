@@ -76,8 +76,8 @@ struct clb_sim {
     size_t buf_bytes = 0;
     void* buf[2] = {nullptr, nullptr};
     int cur = 0;            // buffer holding the last completed step
-    double* obs = nullptr;  // device scratch of the observable reductions: L.total doubles, the
-                            // wait-status word's copy, the reduction's block counter
+    double* obs = nullptr;  // device scratch of the observable reductions: L.total doubles, a
+                            // spare slot, the reduction's block counter
     double* hobs = nullptr; // pinned host copy of the first L.total + 1
     unsigned* status = nullptr;  // error bits of bounded device waits
     int pipeline = 1;       // 1 direct loads, 2.. TMA-staged tile shapes
@@ -931,17 +931,20 @@ clb_status clb_observables(clb_sim* s, int profile_col, clb_scalars* sc, double*
     const double gx = s->drive == CLB_DRIVE_BODY_FORCE ? s->g : 0.0;
     dim3 block(kObsCols, kObsRows);
     dim3 grid(s->L.nblocks);
-    // one launch: the last block sums the partials and takes the status word;
-    // its counter (after the status slot) is cleared first, in case an
-    // earlier launch did not finish
+    // one launch: the last block sums the partials into part[0..3] and puts
+    // the status word at part[4] (block 1's partial, no longer needed, or the
+    // spare slot at L.total when there is one block), so that everything the
+    // host needs is one contiguous range; its counter (after the spare slot) is
+    // cleared first, in case an earlier launch did not finish
     unsigned* done = reinterpret_cast<unsigned*>(s->obs + s->L.total + 1);
+    double* status_out = s->obs + s->L.part + 4;
     CUDA_OR(cudaMemsetAsync(done, 0, sizeof(unsigned), s->stream));
     CUDA_OR(with_storage(s->storage, [&](auto tag) {
         using T = decltype(tag);
         auto args = [&](auto kern) {
             kern<<<grid, block, 0, s->stream>>>(static_cast<const T*>(s->buf[s->cur]), s->obs, s->L, nx, ny, s->pitch,
                                                 s->xoff, s->plane, s->ref0, s->ref_slope, gx, 0.0, profile_col,
-                                                1.0 / s->store_scale, done, s->status, s->obs + s->L.total);
+                                                1.0 / s->store_scale, done, s->status, status_out);
         };
         if (s->drive == CLB_DRIVE_BODY_FORCE)
             args(obs_kernel<T, true>);
@@ -949,16 +952,14 @@ clb_status clb_observables(clb_sim* s, int profile_col, clb_scalars* sc, double*
             args(obs_kernel<T, false>);
         return cudaGetLastError();
     }));
-    // one pinned copy of what is asked for, one synchronisation: the column
-    // arrays (m(x), centre density) only if an output needs them; the
-    // profiles, the partial sums and the status word always
+    // one pinned copy of what is asked for, one synchronisation: from the
+    // column arrays (m(x), centre density; only if an output needs them) or
+    // from the profiles, through the summed partials and the status word
     double* h = s->hobs;
     const bool cols = p_centre || dp_nonlin || m_of_x;
-    if (cols)
-        CUDA_OR(cudaMemcpyAsync(h, s->obs, (size_t)2 * nx * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
-    CUDA_OR(cudaMemcpyAsync(h + s->L.prof_x, s->obs + s->L.prof_x, ((size_t)2 * ny + 4) * sizeof(double),
-                            cudaMemcpyDeviceToHost, s->stream));
-    CUDA_OR(cudaMemcpyAsync(h + s->L.total, s->obs + s->L.total, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    const size_t first = cols ? 0 : s->L.prof_x, last = s->L.part + 5;
+    CUDA_OR(cudaMemcpyAsync(h + first, s->obs + first, (last - first) * sizeof(double), cudaMemcpyDeviceToHost,
+                            s->stream));
     CUDA_OR(cudaStreamSynchronize(s->stream));
 
     const double* hm = h + s->L.m;
@@ -967,7 +968,7 @@ clb_status clb_observables(clb_sim* s, int profile_col, clb_scalars* sc, double*
     const double* huy = h + s->L.prof_y;
     const double msum = h[s->L.part + 0], usum = h[s->L.part + 1], mass = h[s->L.part + 2];
     const double nbad = h[s->L.part + 3];
-    const unsigned wait_bits = (unsigned)h[s->L.total];
+    const unsigned wait_bits = (unsigned)h[s->L.part + 4];
     const double p_in = s->rho_in / 3.0, p_out = s->rho_out / 3.0;
     const double L = nx > 1 ? (double)(nx - 1) : 1.0;
     if (cols) {
