@@ -121,7 +121,12 @@ __global__ void __launch_bounds__(NC + 32, MB) sweep_tma_kernel(const SweepArgs 
             return;
         }
         const T* stage = reinterpret_cast<const T*>(smem + s * G::STAGE_BYTES);
-        tile_update<T, MODE, V, G::SEG>(a, c, stage, tcx * V, xt * G::W + tcx * V, y, empty + s, src, fout);
+        // most tiles are plain: an interior row, neither end column (the
+        // first and the last tile of a row hold those)
+        if (row_kind(y, a.ny) == 0 && xt != 0 && xt != tiles_per_row - 1)
+            tile_update<T, MODE, V, G::SEG, true>(a, c, stage, tcx * V, xt * G::W + tcx * V, y, empty + s, src, fout);
+        else
+            tile_update<T, MODE, V, G::SEG, false>(a, c, stage, tcx * V, xt * G::W + tcx * V, y, empty + s, src, fout);
     }
 }
 

@@ -179,18 +179,22 @@ __device__ __forceinline__ void load_tile(const SweepArgs& a, const Field<T> f, 
 // field `dst` (periodic channels also write the halo columns -1 and nx).
 // c: the constants in the units of the stored values (SweepArgs::ks), so
 // 16-bit values are converted without a scale multiply.
-template <class T, int MODE, int V, int SEG>
+// kPlain: the tile lies in an interior row and holds neither column 0 nor
+// column nx - 1 (nor columns past nx - 1): the copy of this code for such
+// tiles, most of them, has no wall, end-column or ragged-edge branches.
+template <class T, int MODE, int V, int SEG, bool kPlain>
 __device__ __forceinline__ void tile_update(const SweepArgs& a, const KC<typename Codec<T>::R>& c, const T* stage,
                                             int sv, int x0, int y, uint64_t* empty, const Field<T> src,
                                             T* dst) {
     using R = typename Codec<T>::R;
-    const int rt = row_kind(y, a.ny);
+    const int rt = kPlain ? 0 : row_kind(y, a.ny);
     constexpr int E = 16 / (int)sizeof(T);
     constexpr bool kShift = (MODE == MODE_PRESSURE) && !std::is_same<T, double>::value;
     // The thread's window of slot i, columns x0 - 1 .. x0 + V (index k + 1):
     // the V middle values in one aligned vector load, an end value only for the
-    // slots that pull from it (e_x = +1 from the left, e_x = -1 from the right;
-    // the wall rows pull slots 5-8 from both sides).
+    // slots that pull from it (e_x = +1 from the left: 1, 5, 8; e_x = -1 from
+    // the right: 3, 6, 7; a wall row's CBBSR also takes 6 and 7 from the left
+    // and 5 and 8 from the right).
     using VT = typename VecT<T, V>::type;
     R w[9][V + 2];
 #pragma unroll
@@ -210,8 +214,10 @@ __device__ __forceinline__ void tile_update(const SweepArgs& a, const KC<typenam
 #pragma unroll
             for (int k = 0; k < V; ++k) w[i][k + 1] = Raw<T>::dec(e[k]);
         }
-        w[i][0] = (i == 1 || i >= 5) ? Raw<T>::dec(p[-1]) : R(0);
-        w[i][V + 1] = (i == 3 || i >= 5) ? Raw<T>::dec(p[V]) : R(0);
+        const bool left = i == 1 || i == 5 || i == 8 || (!kPlain && (i == 6 || i == 7));
+        const bool right = i == 3 || i == 6 || i == 7 || (!kPlain && (i == 5 || i == 8));
+        w[i][0] = left ? Raw<T>::dec(p[-1]) : R(0);
+        w[i][V + 1] = right ? Raw<T>::dec(p[V]) : R(0);
     }
     // element of slot i at column x0 + k (k may be -1 .. V)
     auto at = [&](int i, int k) -> R { return w[i][k + 1]; };
@@ -253,12 +259,12 @@ __device__ __forceinline__ void tile_update(const SweepArgs& a, const KC<typenam
         }
     }
     mbar_arrive(empty);  // the stage's data is in registers now
-    if (x0 >= a.nx) return;
+    if (!kPlain && x0 >= a.nx) return;
 
     // the thread's node in the first and in the last column, if any (x0 < nx)
-    const int kfirst = x0 == 0 ? 0 : -1;
-    const int klast = a.nx - 1 - x0 < V ? a.nx - 1 - x0 : -1;
-    if (MODE == MODE_PRESSURE) {
+    const int kfirst = !kPlain && x0 == 0 ? 0 : -1;
+    const int klast = !kPlain && a.nx - 1 - x0 < V ? a.nx - 1 - x0 : -1;
+    if (MODE == MODE_PRESSURE && !kPlain) {
         const int kin = kfirst, kout = klast;  // inlet x = 0, outlet x = nx - 1
         if (kin >= 0) {
             R t[9];
@@ -316,7 +322,7 @@ __device__ __forceinline__ void tile_update(const SweepArgs& a, const KC<typenam
     }
     const long long P = a.plane;
     T* orow = dst + (long long)y * a.pitch + a.xoff;
-    if (x0 + V <= a.nx) {
+    if (kPlain || x0 + V <= a.nx) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             VT v;
@@ -340,7 +346,7 @@ __device__ __forceinline__ void tile_update(const SweepArgs& a, const KC<typenam
 #pragma unroll
                 for (int i = 0; i < 9; ++i) orow[i * P + x0 + k] = Raw<T>::enc(f[i][k]);
     }
-    if (MODE == MODE_PERIODIC) {
+    if (MODE == MODE_PERIODIC && !kPlain) {
         // column 0 is mirrored into the halo column nx, column nx - 1 into -1
 #pragma unroll
         for (int k = 0; k < V; ++k) {
