@@ -492,8 +492,8 @@ def errors_vs_oracle(clb, variants, ref, steps):
     return out
 
 
-# tile shapes of the TMA-staged sweep, pipelines 2 and 3: (consumer threads, nodes per thread, stages)
-TMA_SHAPES = [(512, 2, 3), (256, 4, 3)]
+# tile shapes of the TMA-staged sweep, pipelines 2 to 4: (consumer threads, nodes per thread, stages)
+TMA_SHAPES = [(512, 2, 3), (256, 4, 3), (224, 4, 3)]
 
 
 def engine_of(pipeline: int) -> dict:

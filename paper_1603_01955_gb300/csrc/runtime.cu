@@ -635,8 +635,8 @@ clb_status clb_create(int nx, int ny, double kn, double a, double r, clb_drive d
     s->withhold_tile = o.test_withhold_tile;
     // Default engine: the TMA tile shape that was fastest on the 25601 x 256
     // pressure channel for the storage (pipeline 2: 512 x 2 nodes, 3 stages,
-    // for FP32; pipeline 3: 256 x 4 nodes, 3 stages, for 16-bit).  Below 2^20
-    // nodes, where a step is
+    // for FP32; 3: 256 x 4 nodes, 3 stages, for FP16; 4: 224 x 4 nodes, 3
+    // stages, for BF16).  Below 2^20 nodes, where a step is
     // bound by its latency rather than by HBM, the direct-load sweep is faster
     // (801 x 8: 4.1 against 4.7 us; 6401 x 64: 6.4 against 7.5 us per step),
     // and from 12801 x 128 up the TMA sweep is.  FP64 and the centreline
@@ -648,7 +648,7 @@ clb_status clb_create(int nx, int ny, double kn, double a, double r, clb_drive d
     else if ((long long)nx * ny < (1LL << 20))
         s->pipeline = 1;  // small channels: the direct sweep has the shorter latency per step
     else
-        s->pipeline = (o.storage == CLB_FP32_SHIFTED) ? 2 : 3;
+        s->pipeline = (o.storage == CLB_FP32_SHIFTED) ? 2 : (o.storage == CLB_FP16_SCALED) ? 3 : 4;
     {
         // graph replay: not with the testing option
         int k = 0;

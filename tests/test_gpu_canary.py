@@ -80,7 +80,7 @@ CASES = [
     ("fp64", (1,), 0),
     ("fp32s", (1, 2, 3), 0),
     ("fp16s", (1, 3, 2), 0),
-    ("bf16s", (3,), 0),
+    ("bf16s", (4, 3), 0),
     ("fp32s", (1,), 1),
 ]
 

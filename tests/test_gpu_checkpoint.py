@@ -28,7 +28,7 @@ CASES = [
     ("fp32s", "pressure", 0, 0, 1),
     ("fp32s", "body_force", 0, 2, 3),
     ("fp16s", "pressure", 0, 0, 0),
-    ("bf16s", "body_force", 0, 0, 2),
+    ("bf16s", "body_force", 0, 4, 2),
     ("fp32s", "pressure", 1, 0, 0),
     ("fp64", "pressure", 1, 0, 0),
 ]
