@@ -226,12 +226,15 @@ def run_gpu(args):
         info = ch.info()
         stream = ch.stream
         with torch.cuda.stream(stream):
-            ch.step(W)
-            ch.observables()
+            ch.observables()  # first call: the reduction's buffers and the residual history
             ch.sync()
             e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            # the clock sampler starts first (it waits for nvidia-smi), so that the
+            # W warm-up steps run directly before the timed region: an idle GPU
+            # takes about 1 us per sweep longer over a short region
             sampler = ClockSampler(sampler_id)
             with sampler:
+                ch.step(W)
                 barrier()
                 torch.cuda.synchronize()
                 e0.record(stream)
