@@ -155,16 +155,20 @@ __global__ void init_kernel(T* f, int nx, int ny, int pitch, int xoff, long long
 // reference are worked out once per row, and both sides are read and written
 // along x, so `out` / `in` may also be host memory the device can reach
 // (pinned, mapped).
+// Written in the output's memory order over a flat grid (as from_canonical
+// reads): into pinned host memory this keeps the link busiest.
 template <class T>
 __global__ void to_canonical_kernel(const T* f, double* out, int nx, int ny, int pitch, int xoff, long long plane,
                                     double ref0, double ref_slope, double isc) {
-    for (int row = blockIdx.y; row < 9 * ny; row += gridDim.y) {
-        const int i = row / ny, y = row - i * ny;
+    const long long n = 9LL * ny * nx;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long row = idx / nx;
+        const int x = (int)(idx - row * nx);
+        const int i = (int)(row / ny), y = (int)(row - (long long)i * ny);
         const T* src = f + i * plane + (long long)y * pitch + xoff;
-        double* dst = out + (long long)row * nx;
         const double wr0 = c_w[i] * ref0, wrs = c_w[i] * ref_slope;
-        for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < nx; x += gridDim.x * blockDim.x)
-            dst[x] = fma(wrs, (double)x, wr0) + (double)Codec<T>::dec(src[x], RT<T>(isc));
+        out[idx] = fma(wrs, (double)x, wr0) + (double)Codec<T>::dec(src[x], RT<T>(isc));
     }
 }
 
@@ -857,17 +861,12 @@ clb_status clb_info(const clb_sim* s, clb_info_t* info) {
     return CLB_OK;
 }
 
-// Grid of the row-wise conversion kernels.
-// Grid of the flat conversion: eight 256-thread blocks per SM.
+// Grid of the flat conversion kernels: eight 256-thread blocks per SM.
 static int flat_grid() {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     return 8 * std::max(sms, 1);
-}
-
-static dim3 canon_grid(int nx, int ny) {
-    return dim3((unsigned)std::min(8, (nx + 255) / 256), (unsigned)std::min(9 * ny, 65535));
 }
 
 // The device's address of a host array, if the device can reach it (pinned
@@ -893,7 +892,7 @@ clb_status clb_get_state(clb_sim* s, double* host_f) {
     clb_status st = CLB_OK;
     cudaError_t e = with_storage(s->storage, [&](auto tag) {
         using T = decltype(tag);
-        to_canonical_kernel<T><<<canon_grid(s->nx, s->ny), 256, 0, s->stream>>>(
+        to_canonical_kernel<T><<<flat_grid(), 256, 0, s->stream>>>(
             static_cast<const T*>(s->buf[s->cur]), tmp, s->nx, s->ny, s->pitch, s->xoff, s->plane, s->ref0,
             s->ref_slope, 1.0 / s->store_scale);
         return cudaGetLastError();
