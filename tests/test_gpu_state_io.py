@@ -1,7 +1,10 @@
 """clb_set_state / clb_get_state with pinned host arrays (read and written by
-the conversion kernels directly) and with ordinary pageable arrays (staged
-through a device buffer) give the same bits, for every storage and both
-drives (the periodic channel also fills its halo columns on the way in)."""
+the conversion kernels directly, walking the FP64 array in its memory order)
+and with ordinary pageable arrays (staged through a device buffer, walked row
+by row) give the same bits, for every storage and both drives (the periodic
+channel also fills its halo columns on the way in), on shapes from one node to
+states of several grid strides (each thread of the flat walk then steps more
+than once, across row ends, and with nx wider than a stride)."""
 import numpy as np
 import pytest
 
@@ -23,10 +26,10 @@ def clb():
 
 @pytest.mark.parametrize("storage", ["fp64", "fp32s", "fp16s", "bf16s"])
 @pytest.mark.parametrize("drive,value", [("pressure", 1.7), ("body_force", 3e-5)])
-def test_pinned_and_pageable_state_io_agree(clb, storage, drive, value):
+@pytest.mark.parametrize("nx,ny", [(777, 13), (4, 1), (4097, 64), (400001, 2)])
+def test_pinned_and_pageable_state_io_agree(clb, storage, drive, value, nx, ny):
     import torch
 
-    nx, ny = 777, 13
     ch = clb.Channel(nx, ny, 0.2, drive=drive, drive_value=value, storage=storage)
     f0 = inputs.perturb(inputs.rng(nx + ny), ch.state(), 0.05)
     pin_in = torch.empty((9, ny, nx), dtype=torch.float64, pin_memory=True)
