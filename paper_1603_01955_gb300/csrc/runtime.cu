@@ -78,7 +78,8 @@ struct clb_sim {
     int cur = 0;            // buffer holding the last completed step
     double* obs = nullptr;  // device scratch of the observable reductions: L.total doubles, a
                             // spare slot, the reduction's block counter
-    double* hobs = nullptr; // pinned host copy of the first L.total + 1
+    double* hobs = nullptr; // pinned host copy of the first L.total + 1; slot L.total + 1 holds
+                            // the status word read by check_status
     unsigned* status = nullptr;  // error bits of bounded device waits
     int pipeline = 1;       // 1 direct loads, 2.. TMA-staged tile shapes
     int withhold_tile = -1; // testing: TMA tile withheld in the first launch
@@ -773,7 +774,7 @@ clb_status clb_create(int nx, int ny, double kn, double a, double r, clb_drive d
     s->buf[0] = s->dalloc(s->buf_bytes);
     s->buf[1] = s->dalloc(s->buf_bytes);
     s->obs = static_cast<double*>(s->dalloc((s->L.total + 2) * sizeof(double)));
-    if (cudaHostAlloc(reinterpret_cast<void**>(&s->hobs), (s->L.total + 1) * sizeof(double), cudaHostAllocDefault) !=
+    if (cudaHostAlloc(reinterpret_cast<void**>(&s->hobs), (s->L.total + 2) * sizeof(double), cudaHostAllocDefault) !=
         cudaSuccess) {
         cudaGetLastError();
         s->hobs = nullptr;
@@ -865,9 +866,11 @@ clb_status clb_step(clb_sim* s, int64_t n) {
 
 // Read and clear the device status word; CLB_ETIMEOUT if a wait expired.
 static clb_status check_status(clb_sim* s, const char* who) {
-    unsigned st = 0;
-    CUDA_OR(cudaMemcpyAsync(&st, s->status, sizeof st, cudaMemcpyDeviceToHost, s->stream));
+    // into pinned memory: a copy to pageable memory would be staged by the driver
+    unsigned* hst = reinterpret_cast<unsigned*>(s->hobs + s->L.total + 1);
+    CUDA_OR(cudaMemcpyAsync(hst, s->status, sizeof *hst, cudaMemcpyDeviceToHost, s->stream));
     CUDA_OR(cudaStreamSynchronize(s->stream));
+    const unsigned st = *hst;
     if (st) {
         CUDA_OR(cudaMemsetAsync(s->status, 0, sizeof(unsigned), s->stream));
         return fail(CLB_ETIMEOUT, "%s: a sweep gave up waiting for its staged inputs (bits %u)", who, st);
@@ -877,7 +880,8 @@ static clb_status check_status(clb_sim* s, const char* who) {
 
 clb_status clb_sync(clb_sim* s) {
     if (!s) return fail(CLB_EINVAL, "clb_sync: sim is NULL");
-    CUDA_OR(cudaStreamSynchronize(s->stream));
+    // the status copy is queued behind all of the stream's work, so the one
+    // synchronisation in check_status waits for everything
     return check_status(s, "clb_sync");
 }
 
