@@ -140,14 +140,24 @@ cudaError_t launch_tma_one(const SweepArgs& a, cudaStream_t st, unsigned* status
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    int dev = 0, sms = 0, per_sm = 0;
+    // resident blocks (SMs x blocks per SM), worked out once per device: the
+    // occupancy query would otherwise add host time to every launch
+    constexpr int kMaxDevices = 64;
+    static int resident[kMaxDevices] = {};  // per instantiation
+    int dev = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NC + 32, G::SMEM);
-    if (e != cudaSuccess) return e;
+    int slots = (dev >= 0 && dev < kMaxDevices) ? resident[dev] : 0;
+    if (slots == 0) {
+        int sms = 0, per_sm = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NC + 32, G::SMEM);
+        if (e != cudaSuccess) return e;
+        slots = max(1, per_sm) * sms;
+        if (dev >= 0 && dev < kMaxDevices) resident[dev] = slots;
+    }
     const int tiles_per_row = (a.nx + G::W - 1) / G::W;
     const int ntiles = tiles_per_row * a.ny;
-    const int grid = min(ntiles, max(1, per_sm) * sms);
+    const int grid = min(ntiles, slots);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(NC + 32);
