@@ -496,7 +496,7 @@ def errors_vs_oracle(clb, variants, ref, steps):
 
 
 # tile shapes of the TMA-staged sweep, pipelines 2 to 4: (consumer threads, nodes per thread, stages)
-TMA_SHAPES = [(512, 2, 3), (256, 4, 3), (224, 4, 3)]
+TMA_SHAPES = [(512, 2, 3), (128, 4, 2), (256, 4, 3)]
 
 
 def engine_of(pipeline: int) -> dict:

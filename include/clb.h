@@ -83,12 +83,13 @@ typedef struct {
     void* alloc_ctx;
     /* How the sweep reads its inputs (FP32 and 16-bit storage; FP64 and
      * kn_mode 1 always 1): 0 = default (1 for channels below 2^20 nodes;
-     * larger ones 2 for FP32_SHIFTED, 3 for FP16_SCALED, 4 for BF16_SCALED),
+     * larger ones 2 for FP32_SHIFTED, 3 for FP16_SCALED and BF16_SCALED),
      * 1 = direct vector loads with warp shuffles (the only engine that vec and
      * block_x configure), 2..4 = staged through shared memory by TMA bulk
      * copies, tile shape 0..2 of the table in sweep_tma.cu (2: 512 consumer
-     * threads x 2 nodes, 3 stages; 3: 256 x 4 nodes, 3 stages; 4: 224 x 4
-     * nodes, 3 stages).  All give bit-identical results. */
+     * threads x 2 nodes, 3 stages; 3: 128 x 4 nodes, 2 stages; 4: 256 x 4
+     * nodes, 3 stages), tiles claimed dynamically by the blocks of a
+     * persistent grid.  All give bit-identical results. */
     int pipeline;
     /* Local Knudsen number of a pressure channel (Sec. 3.2): 0 = from the
      * node's own pressure (default), 1 = from the centreline pressure p(x) of

@@ -108,9 +108,11 @@ cudaError_t launch_sweep(int storage, int mode, int vec, int block_x, const Swee
 bool sweep_supported(int storage, int vec);
 
 // The sweep with TMA-staged inputs (FP32 and 16-bit storage); variant picks
-// the tile shape.  *status collects error bits of bounded waits that expired.
+// the tile shape.  sched: two device counters, zero between launches (zero
+// them once after allocation; each launch leaves them zero again).  *status
+// collects error bits of bounded waits that expired.
 cudaError_t launch_sweep_tma(int storage, int mode, int variant, const SweepArgs& a, cudaStream_t stream,
-                             unsigned* status);
+                             unsigned* sched, unsigned* status);
 int tma_variant_count();
 
 }  // namespace clb

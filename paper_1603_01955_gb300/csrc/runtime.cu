@@ -81,6 +81,7 @@ struct clb_sim {
     double* hobs = nullptr; // pinned host copy of the first L.total + 1; slot L.total + 1 holds
                             // the status word read by check_status
     unsigned* status = nullptr;  // error bits of bounded device waits
+    unsigned* sched = nullptr;   // TMA sweep: tile claim counters (2), zero between launches
     int pipeline = 1;       // 1 direct loads, 2.. TMA-staged tile shapes
     int withhold_tile = -1; // testing: TMA tile withheld in the first launch
     int graph_steps = 0;    // sweeps per replayed CUDA graph (0: no replay); even
@@ -623,6 +624,7 @@ clb_status clb_destroy(clb_sim* s) {
     s->dfree(s->obs);
     if (s->hobs) cudaFreeHost(s->hobs);
     s->dfree(s->status);
+    s->dfree(s->sched);
     s->dfree(s->rc);
     for (cudaGraphExec_t g : s->graph)
         if (g) cudaGraphExecDestroy(g);
@@ -690,8 +692,8 @@ clb_status clb_create(int nx, int ny, double kn, double a, double r, clb_drive d
     s->withhold_tile = o.test_withhold_tile;
     // Default engine: the TMA tile shape that was fastest on the 25601 x 256
     // pressure channel for the storage (pipeline 2: 512 x 2 nodes, 3 stages,
-    // for FP32; 3: 256 x 4 nodes, 3 stages, for FP16; 4: 224 x 4 nodes, 3
-    // stages, for BF16).  Below 2^20 nodes, where a step is
+    // for FP32; 3: 128 x 4 nodes, 2 stages, 4 blocks per SM, for FP16 and
+    // BF16).  Below 2^20 nodes, where a step is
     // bound by its latency rather than by HBM, the direct-load sweep is faster
     // (801 x 8: 4.1 against 4.7 us; 6401 x 64: 6.4 against 7.5 us per step),
     // and from 12801 x 128 up the TMA sweep is.  FP64 and the centreline
@@ -703,7 +705,7 @@ clb_status clb_create(int nx, int ny, double kn, double a, double r, clb_drive d
     else if ((long long)nx * ny < (1LL << 20))
         s->pipeline = 1;  // small channels: the direct sweep has the shorter latency per step
     else
-        s->pipeline = (o.storage == CLB_FP32_SHIFTED) ? 2 : (o.storage == CLB_FP16_SCALED) ? 3 : 4;
+        s->pipeline = (o.storage == CLB_FP32_SHIFTED) ? 2 : 3;
     {
         // graph replay: not with the testing option
         int k = 0;
@@ -780,9 +782,10 @@ clb_status clb_create(int nx, int ny, double kn, double a, double r, clb_drive d
         s->hobs = nullptr;
     }
     s->status = static_cast<unsigned*>(s->dalloc(sizeof(unsigned)));
+    s->sched = static_cast<unsigned*>(s->dalloc(2 * sizeof(unsigned)));
     s->rc_stride = ((nx + 16 + 31) / 32) * 32;
     s->rc = s->dalloc((size_t)4 * s->rc_stride * (o.storage == CLB_FP64 ? 8 : 4));
-    if (!s->buf[0] || !s->buf[1] || !s->obs || !s->hobs || !s->status || !s->rc) {
+    if (!s->buf[0] || !s->buf[1] || !s->obs || !s->hobs || !s->status || !s->sched || !s->rc) {
         clb_destroy(s);
         return fail(CLB_ENOMEM, "clb_create: device allocation of %zu bytes failed", 2 * s->buf_bytes);
     }
@@ -794,6 +797,7 @@ clb_status clb_create(int nx, int ny, double kn, double a, double r, clb_drive d
     chk(cudaMemsetAsync(s->buf[1], 0, s->buf_bytes, s->stream), "memset");
     chk(cudaMemsetAsync(s->obs, 0, (s->L.total + 2) * sizeof(double), s->stream), "memset");
     chk(cudaMemsetAsync(s->status, 0, sizeof(unsigned), s->stream), "memset");
+    chk(cudaMemsetAsync(s->sched, 0, 2 * sizeof(unsigned), s->stream), "memset");
     const double rho_slope = (drive == CLB_DRIVE_PRESSURE) ? (s->rho_out - s->rho_in) / (double)(nx - 1) : 0.0;
     chk(cudaMemsetAsync(s->rc, 0, (size_t)4 * s->rc_stride * (o.storage == CLB_FP64 ? 8 : 4), s->stream), "memset");
     chk(launch_init(s, s->buf[0], s->rho_in, rho_slope), "init");
@@ -815,7 +819,7 @@ static cudaError_t launch_single(clb_sim* s, SweepArgs& a, int mode, int cur) {
     a.rc_in = static_cast<const char*>(s->rc) + cur * rc_side;
     a.rc_out = static_cast<char*>(s->rc) + (cur ^ 1) * rc_side;
     a.tile_order = cur;  // alternate the TMA sweep's tile order with the buffers
-    return s->pipeline >= 2 ? launch_sweep_tma(s->storage, mode, s->pipeline - 2, a, s->stream, s->status)
+    return s->pipeline >= 2 ? launch_sweep_tma(s->storage, mode, s->pipeline - 2, a, s->stream, s->sched, s->status)
                             : launch_sweep(s->storage, mode, s->vec, s->block_x, a, s->stream);
 }
 

@@ -1,9 +1,10 @@
-"""The TMA-staged sweep (pipelines 2 to 4, its three tile shapes) against the
-direct-load sweep (pipeline 1): node for node the same arithmetic, so the
-states must agree bit for bit, on random perturbed states, ragged sizes
-(tiles of 1024 and 896 columns, rows of one node, channels shorter than one
-tile), odd and even step counts, both drives and every non-FP64 storage.  The
-direct sweep itself is checked against the oracle in test_gpu_parity.py."""
+"""The TMA-staged sweep (pipelines 2 to 4, its three tile shapes, tiles
+claimed in whatever order the blocks reach them) against the direct-load
+sweep (pipeline 1): node for node the same arithmetic, so the states must
+agree bit for bit, on random perturbed states, ragged sizes (tiles of 1024
+and 512 columns, rows of one node, channels shorter than one tile), odd and
+even step counts, both drives and every non-FP64 storage.  The direct sweep
+itself is checked against the oracle in test_gpu_parity.py."""
 import numpy as np
 import pytest
 
@@ -82,7 +83,7 @@ def test_tma_many_launches(clb, storage, nx, ny, drive):
 
 
 @pytest.mark.parametrize("storage,kn_mode,want", [("fp64", 0, 1), ("fp32s", 0, 2), ("fp16s", 0, 3),
-                                                  ("bf16s", 0, 4), ("fp32s", 1, 1)])
+                                                  ("bf16s", 0, 3), ("fp32s", 1, 1)])
 def test_default_engine(clb, storage, kn_mode, want):
     """TMA shapes for channels of 2^20 nodes and more, the direct sweep below."""
     ch = clb.Channel(4097, 256, 0.2, drive="pressure", drive_value=1.5, storage=storage, kn_mode=kn_mode)

@@ -39,7 +39,8 @@ def make(clb, storage, drive, kn_mode, pipeline, graph_steps):
 
 @pytest.mark.parametrize("storage,drive,kn_mode,pipeline", [("fp32s", "pressure", 0, 0), ("fp32s", "body_force", 0, 1),
                                                           ("fp16s", "pressure", 0, 0), ("fp64", "pressure", 0, 0),
-                                                          ("fp32s", "pressure", 1, 0)])
+                                                          ("fp32s", "pressure", 1, 0), ("fp16s", "pressure", 0, 3),
+                                                          ("fp32s", "body_force", 0, 2)])
 def test_replayed_chunks_equal_single_launches(clb, storage, drive, kn_mode, pipeline):
     f0 = None
     states = []
