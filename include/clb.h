@@ -377,10 +377,11 @@ clb_status clb_adjoint_destroy(clb_adjoint* h);
  * address (cudaGetSymbolAddress) with the device current; make that first call
  * before any stream capture.  The address is kept for the life of the process:
  * after cudaDeviceReset (or anything else that destroys the device's primary
- * context) it is stale, so do not call this entry point on that device again.  All calls on a device share the array: calls that
- * overlap on the GPU (from several streams or threads at once) race and give
- * wrong results; serialise them.  The array keeps the last call's contents, and
- * each call clears the part it uses before reducing.
+ * context) it is stale, so do not call this entry point on that device again.
+ * All calls on a device share the array: calls that overlap on the GPU (from
+ * several streams or threads at once) race and give wrong results; serialise
+ * them.  The array keeps the last call's contents, and each call clears the
+ * part it uses before reducing.
  * Errors: CLB_EINVAL, CLB_ECUDA, CLB_ENUMERIC (non-finite field, outputs written).
  */
 clb_status clb_observables_noalloc(const double* f_dev, int nx, int ny, int drive, double g, double rho_in,
