@@ -586,7 +586,9 @@ clb_status clb_batch_create(int n, const int* nx, const int* ny, const double* k
     const size_t elem = o.storage == CLB_FP64 ? 8 : 4;
     int max_nodes = 0;
     for (int k = 0; k < n; ++k) {
-        if (nx[k] < 1 || ny[k] < 1 || !(kn[k] > 0) || !std::isfinite(kn[k]))
+        // a block holds a whole channel (at most 8 x 512 nodes), so larger
+        // sides are rejected here, before their product can overflow
+        if (nx[k] < 1 || ny[k] < 1 || nx[k] > 8 * 512 || ny[k] > 8 * 512 || !(kn[k] > 0) || !std::isfinite(kn[k]))
             return (clb_status)set_error(CLB_EINVAL, "clb_batch_create: channel %d: bad nx, ny or Kn", k);
         max_nodes = std::max(max_nodes, nx[k] * ny[k]);
     }
