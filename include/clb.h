@@ -29,6 +29,10 @@
  *     clb_last_error() gives a message for the last failure on the calling
  *     thread.
  *   - A simulation may be used from one host thread at a time.
+ *   - A simulation (batch, adjoint handle) lives on the device that was
+ *     current when it was created, as its stream and buffers do; make that
+ *     device current before every call on it.  The library does not switch
+ *     devices itself.
  */
 #ifndef CLB_H
 #define CLB_H
