@@ -340,9 +340,11 @@ def test_pressure_channel_continuum_limit(oracle_mod):
     isothermal lubrication solution with a pressure-independent viscosity
     (mean free path inversely proportional to pressure) has p(x)^2 linear in x
     and mass flow m_ns; slip raises S = m/m_ns a little above 1 and bends p(x)
-    a little less.  So S lies in (1, 1.25) and the centreline pressure follows
+    a little less.  So S lies in (1, 1.25), and the centreline pressure follows
     the no-slip p(x) to within a fifth of that profile's departure from the
-    straight line."""
+    straight line; the non-linear pressure deviation (p - p_l)/p_out of
+    Sec. 3.2 follows the same profile's (p_lub - p_l)/p_out to within a fifth
+    of its size."""
     nx, ny, ratio = 401, 8, 1.5
     p = oracle_mod.OracleParams(nx=nx, ny=ny, pressure=True, kn=0.02, rho_in=ratio)
     s = oracle_mod.OracleSim(p)
@@ -355,3 +357,5 @@ def test_pressure_channel_continuum_limit(oracle_mod):
     p_lin = p_in - (p_in - p_out) * x
     bend = np.abs(p_lub - p_lin).max()
     assert np.abs(o["p_centre"] - p_lub).max() < 0.2 * bend
+    dp_lub = (p_lub - p_lin) / p_out
+    assert np.abs(o["dp_nonlin"] - dp_lub).max() < 0.2 * dp_lub.max()

@@ -74,6 +74,15 @@ MUTANTS = [
     ("q_norm_sqrt_RT", "(3.0 * P_gx(p) * (double)ny * (double)ny * sqrt(1.0 / 6.0))",
      "(3.0 * P_gx(p) * (double)ny * (double)ny * sqrt(1.0 / 3.0))"),
     ("m_ns_constant", "(24.0 * mu * (1.0 / 3.0) * L)", "(12.0 * mu * (1.0 / 3.0) * L)"),
+    ("m_ns_height_squared", "(double)ny * ny * ny * (p_in * p_in - p_out * p_out)",
+     "(double)ny * ny * (p_in * p_in - p_out * p_out)"),
+    ("mass_flow_mean_over_rows", "const real_t mbar = msum / (double)nx;", "const real_t mbar = msum / (double)ny;"),
+    ("q_norm_mean_over_rows", "qnorm = (usum / (double)nx)", "qnorm = (usum / (double)ny)"),
+    # observables along the channel (Sec. 3.2): centreline pressure, its non-linear deviation
+    ("centreline_two_rows_summed", "if (ny % 2 == 0 && (y == ny / 2 - 1 || y == ny / 2)) rc += 0.5 * rho;",
+     "if (ny % 2 == 0 && (y == ny / 2 - 1 || y == ny / 2)) rc += rho;"),
+    ("dp_nonlin_over_p_in", "if (dp_nonlin) dp_nonlin[x] = (pc - pl) / p_out;",
+     "if (dp_nonlin) dp_nonlin[x] = (pc - pl) / p_in;"),
     # slip velocity extrapolated to J = 0 instead of the wall at J = 1/2
     ("slip_extrapolated_to_J0_bottom", "const real_t sb = 1.5 * ucol_prof[0] - 0.5 * ucol_prof[1];",
      "const real_t sb = 2.0 * ucol_prof[0] - 1.0 * ucol_prof[1];"),
