@@ -64,6 +64,8 @@ MUTANTS = [
     # pressure columns (Sec. 3.2)
     ("pressure_velocity_not_extrapolated", "oracle_feq(rho_b, 2.0 * u1x - u2x, 2.0 * u1y - u2y, eb);",
      "oracle_feq(rho_b, u1x, u1y, eb);"),
+    ("pressure_nonequilibrium_from_second_column", "out[i] = eb[i] + (f1[i] - e1[i]);",
+     "out[i] = eb[i] + (f2[i] - e1[i]);"),
     ("inlet_gets_outlet_density", "pressure_rebuild(p, a1, a2, p->rho_in, in);",
      "pressure_rebuild(p, a1, a2, p->rho_out, in);"),
     # observables (Sec. 3.1, 3.2)
