@@ -45,6 +45,8 @@ MUTANTS = [
     ("sv_sq_swapped", "s[4] = s[5] = sv; /* Eq. 14: s4 = s5 = s_v */\n    s[6] = s[7] = sq;",
      "s[4] = s[5] = sq;\n    s[6] = s[7] = sv;"),
     ("eq18_constant", "sqrt(6.0 / PI) * (double)ny * kn_local", "sqrt(PI / 6.0) * (double)ny * kn_local"),
+    ("bosanquet_factor_as_one", "(double)ny * kn_local / (1.0 + a * kn_local)",
+     "(double)ny * kn_local / (1.0 + kn_local)"),
     ("eq21_tau_power", "4.0 * PI * tq * tq * b2", "4.0 * PI * tq * b2"),
     ("eq21_B1_of_sigma", "1.0 - 0.1817 * sigma", "1.0 - 0.1817 / sigma"),
     ("local_kn_proportional_to_p", "p->kn * p->rho_out / rho", "p->kn * rho / p->rho_out"),
