@@ -343,6 +343,40 @@ def test_pressure_columns_extrapolate_velocity_linearly(oracle_mod):
         np.testing.assert_allclose(uy[:, b], 2 * uy[:, i1] - uy[:, i2], rtol=0, atol=1e-14)
 
 
+def test_open_ends_pass_a_fully_developed_flow_unchanged(oracle_mod):
+    """A boundary that continues the flow consistently must leave a fully
+    developed flow alone: where the imposed density equals the interior one
+    and nothing varies along x, the rebuilt end column equals its interior
+    neighbour population by population, non-equilibrium part included.
+
+    The state is x-invariant, f = f^eq(rho0, (u(y), 0)) with a sheared u(y).
+    With u_y = 0 the populations moving up (down) carry (M_yy + M_y)/2 = rho0/6
+    in every row, for any u_x, so after streaming and the wall reflections
+    every node of the interior columns again has density rho0, and columns 1
+    and 2 are equal but out of equilibrium (the shear).  With rho_in = rho_out
+    = rho0 the end columns must then reproduce columns 1 and nx-2."""
+    nx, ny, rho0 = 8, 6, 1.0
+    p = oracle_mod.OracleParams(nx=nx, ny=ny, pressure=True, kn=0.1, rho_in=rho0, rho_out=rho0)
+    s = oracle_mod.OracleSim(p)
+    y = np.arange(ny)
+    u = 0.02 * (y + 0.5) * (ny - 0.5 - y) / ny**2 + 0.003 * np.sin(y)
+    f = np.zeros((9, ny, nx))
+    for j in range(ny):
+        f[:, j, :] = np.asarray(oracle_mod.feq(rho0, u[j], 0.0))[:, None]
+    s.set_state(f)
+    fb = s.prestate()
+    np.testing.assert_allclose(fb.sum(axis=0)[:, 1:-1], rho0, rtol=0, atol=1e-15)
+    assert np.abs(fb[:, :, 1] - fb[:, :, 2]).max() <= 1e-16
+    ex, ey = oracle_mod.lattice()
+    c1 = fb[:, :, 1]
+    r1 = c1.sum(axis=0)
+    eq1 = np.stack([np.asarray(oracle_mod.feq(r1[j], ex @ c1[:, j] / r1[j], ey @ c1[:, j] / r1[j]))
+                    for j in range(ny)], 1)
+    assert np.abs(c1 - eq1).max() > 1e-4  # the streamed columns are out of equilibrium
+    np.testing.assert_allclose(fb[:, :, 0], fb[:, :, 1], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(fb[:, :, nx - 1], fb[:, :, nx - 2], rtol=0, atol=1e-15)
+
+
 # ------------------------------------------------------------ continuum limits
 
 @pytest.mark.parametrize("kn", [0.005, 0.01])

@@ -68,6 +68,7 @@ MUTANTS = [
      "oracle_feq(rho_b, u1x, u1y, eb);"),
     ("pressure_nonequilibrium_from_second_column", "out[i] = eb[i] + (f1[i] - e1[i]);",
      "out[i] = eb[i] + (f2[i] - e1[i]);"),
+    ("pressure_columns_in_equilibrium", "out[i] = eb[i] + (f1[i] - e1[i]);", "out[i] = eb[i];"),
     ("inlet_gets_outlet_density", "pressure_rebuild(p, a1, a2, p->rho_in, in);",
      "pressure_rebuild(p, a1, a2, p->rho_out, in);"),
     # observables (Sec. 3.1, 3.2)
