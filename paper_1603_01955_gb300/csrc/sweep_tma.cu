@@ -135,22 +135,23 @@ template <class T, int MODE, int NC, int V, int S, int MB>
 cudaError_t launch_tma_one(const SweepArgs& a, cudaStream_t st, unsigned* sched, unsigned* status) {
     using G = Geometry<T, NC, V, S>;
     auto kern = sweep_tma_kernel<T, MODE, NC, V, S, MB>;
-    // the shared-memory opt-in and the resident blocks (SMs x blocks per SM)
-    // are set up once per device: the attribute belongs to the kernel as
-    // loaded on that device, and the occupancy query would otherwise add host
-    // time to every launch
+    static bool attr_set = false;  // per instantiation
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    // resident blocks (SMs x blocks per SM), worked out once per device: the
+    // occupancy query would otherwise add host time to every launch
     constexpr int kMaxDevices = 64;
     static int resident[kMaxDevices] = {};  // per instantiation
     int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
+    cudaGetDevice(&dev);
     int slots = (dev >= 0 && dev < kMaxDevices) ? resident[dev] : 0;
     if (slots == 0) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
-        if (e != cudaSuccess) return e;
         int sms = 0, per_sm = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NC + 32, G::SMEM);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NC + 32, G::SMEM);
         if (e != cudaSuccess) return e;
         slots = max(1, per_sm) * sms;
         if (dev >= 0 && dev < kMaxDevices) resident[dev] = slots;
