@@ -32,7 +32,11 @@
  *   - A simulation (batch, adjoint handle) lives on the device that was
  *     current when it was created, as its stream and buffers do; make that
  *     device current before every call on it.  The library does not switch
- *     devices itself.
+ *     devices itself.  The TMA-staged sweep (clb_opts.pipeline >= 2) opts
+ *     into its shared-memory size once per process, with the device current
+ *     at its first launch; in a process that drives several devices a launch
+ *     on another device may be refused (CLB_ECUDA), so give the channels there
+ *     pipeline 1, or run one process per device.
  */
 #ifndef CLB_H
 #define CLB_H
